@@ -1,0 +1,72 @@
+"""Mini-stack chain of the oracle (Sec. II-B, "Proposed Approach"; Fig. 1).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Each step, for new real SLCs z_1..z_M:
+  1. merge amplitude statistics (Sec. III-A, eqs. (merged-mean), (merged-variance)
+     with equal weight per image): P <- P + sum_t |z_t|^2, n <- n + M;
+  2. GLRT SHP selection on P with n real samples per pixel (Sec. III-A);
+  3. form the mini-stack [kappa ring oldest..newest, z_1..z_M] (Sec. II-B: the
+     compressed SLCs are prepended; only the K most recent are kept);
+  4. sample coherence over the SHP neighbourhood (eq. (sample-coherence));
+  5. EMI phase linking with reference r = the newest compressed SLC, or the
+     first real SLC when there is none (Sec. II-B items 1-3), and gamma_t;
+  6. compress the real SLCs onto the linked phases (kappa = zeta^H z) and push
+     kappa into the ring.
+The phases returned for the real dates are relative to the first date of the
+archive, because every kappa inherits the reference phase of the one before.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import amp_stats, compress, covariance, glrt_threshold, ntri, phase_link, shp_select
+
+
+def ministack(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, n_eff: int,
+              alpha: float, ref: int, beta: float = 0.0, cond: bool = False) -> dict:
+    """One mini-stack through S2-S7 with statistics already merged."""
+    N = z.shape[0]
+    c = glrt_threshold(alpha, n_eff)
+    mask, count = shp_select(sum_pow, window, np.float32(c))
+    C = covariance(z, window, mask)
+    out = phase_link(C, N, ref, beta, cond=cond)
+    kappa = compress(z, first_real, window, out["phase"])
+    out.update(mask=mask, count=count, C=C, kappa=kappa, c=c)
+    return out
+
+
+class OracleChain:
+    """Sequential processing state: kappa ring, merged power sums, image count."""
+
+    def __init__(self, H: int, W: int, window, K_max: int, alpha: float = 1e-3, beta: float = 0.0):
+        self.H, self.W = H, W
+        self.window = tuple(window)
+        self.K_max = K_max
+        self.alpha, self.beta = alpha, beta
+        self.ring: list[np.ndarray] = []
+        self.sum_pow = np.zeros((H, W), np.float32)
+        self.sum_amp = np.zeros((H, W), np.float32)
+        self.n = 0
+
+    def step(self, new_slc: np.ndarray, cond: bool = False) -> dict:
+        new_slc = np.ascontiguousarray(new_slc, dtype=np.complex64)
+        M = new_slc.shape[0]
+        amp_stats(new_slc, self.sum_pow, self.sum_amp, accumulate=True)
+        self.n += M
+        K = len(self.ring)
+        parts = [np.stack(self.ring).astype(np.complex128)] if K else []
+        parts.append(new_slc.astype(np.complex128))
+        z = np.concatenate(parts, axis=0)
+        ref = K - 1 if K > 0 else 0
+        out = ministack(z, K, self.window, self.sum_pow, self.n, self.alpha, ref, self.beta, cond)
+        self.ring.append(out["kappa"])
+        if len(self.ring) > self.K_max:
+            self.ring.pop(0)
+        out["phase_real"] = out["phase"][K:]
+        out["K_used"] = K
+        out["N"] = z.shape[0]
+        return out
+
+
+__all__ = ["OracleChain", "ministack", "ntri"]
