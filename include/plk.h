@@ -1,0 +1,206 @@
+/*
+ * plk.h -- C ABI of libplk, the GB300 (sm_103a) implementation of the
+ * data-parallel hot path of sequential InSAR phase linking (Staniewicz et al.,
+ * "Near-Real-Time InSAR Phase Estimation for Large-Scale Surface Displacement
+ * Monitoring"): SHP selection on amplitude, SHP-windowed coherence, EMI phase
+ * linking, temporal coherence and compressed-SLC formation under the
+ * always-first mini-stack reference scheme.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Array arguments are DEVICE pointers owned by the caller (for example
+ *    torch tensors), unless a parameter says "host".  The library never frees
+ *    them and never keeps them past the call.
+ *  - Complex samples are plk_c64 (interleaved float re, im; 8-byte aligned).
+ *  - Stacks are date-major and row-major: [N][H][W].  Per-output-pixel arrays
+ *    are [Ho][Wo] (or [N][Ho][Wo] for phases), with, for a window wy x wx and
+ *    strides (sy, sx), Ho = H / sy and Wo = W / sx (integer division), and
+ *    output pixel (i, j) centred on input pixel (i*sy + sy/2, j*sx + sx/2),
+ *    the centre of its sy x sx decimation block (Sec. IV; Supplement S1).
+ *    A window written "X x Y" in the paper has wx = X columns, wy = Y rows.
+ *  - Calls are asynchronous on the context's CUDA stream.  Arguments are
+ *    checked on the host before anything is launched; a bad argument returns
+ *    PLK_EINVAL and launches nothing.  A launch or runtime error returns
+ *    PLK_ECUDA.  plk_last_error() gives a one-line description.
+ *  - Numerical outcomes of single pixels (no data, EVD fallback, ...) are
+ *    data in the status array, not errors.
+ *  - N (entries of one mini-stack, compressed plus real) is 2..PLK_MAX_N.
+ *    Windows are odd, wy*wx <= PLK_MAX_WINDOW.
+ */
+#ifndef PLK_H_
+#define PLK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PLK_MAX_N 32
+#define PLK_MAX_WINDOW 1024
+
+typedef enum plk_status {
+    PLK_OK = 0,
+    PLK_EINVAL = 1,       /* bad argument; nothing was launched */
+    PLK_ENOMEM = 2,       /* a library-owned allocation failed */
+    PLK_ECUDA = 3,        /* CUDA launch/runtime error */
+    PLK_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+    PLK_EUNSUPPORTED = 5  /* valid request this build does not provide */
+} plk_status;
+
+/* Per-pixel outcome codes written to status arrays. */
+enum {
+    PLK_PX_EMI = 0,       /* EMI solution, single precision */
+    PLK_PX_EMI_FP64 = 1,  /* EMI solution re-solved in double precision */
+    PLK_PX_EVD = 2,       /* inversion of |C| failed: EVD fallback (Sec. III-B) */
+    PLK_PX_NODATA = 3,    /* zero-power centre / empty neighbourhood: NaN outputs */
+    PLK_PX_NOCONV = 4     /* inverse iteration hit max_iter; last iterate kept */
+};
+
+typedef struct plk_c64 { float re, im; } plk_c64;
+
+/* SHP search window (odd wy, wx) and output strides (sy, sx >= 1). */
+typedef struct plk_window { int32_t wy, wx, sy, sx; } plk_window;
+
+typedef struct plk_params {
+    double alpha;      /* GLRT size (Sec. III-A), 0 < alpha < 1; default 1e-3 */
+    float beta;        /* |C| regularisation G = (1-beta)|C| + beta I, 0 <= beta < 1;
+                          default 0, the paper's plug-in |C| (Sec. III-B) */
+    float mu;          /* inverse-iteration shift (Sec. III-B); default 0.99 */
+    float tol;         /* stop when the unit iterate moves less than tol (2-norm,
+                          after removing a common phase); default 1e-6 */
+    int32_t max_iter;  /* inverse-iteration cap; default 50 */
+    float cond_max;    /* pixels whose 1-norm condition estimate of G exceeds
+                          cond_max, or whose single-precision inversion of G meets
+                          a pivot below 1e-6, are re-solved in double precision;
+                          default 1e4 */
+    int32_t fp64_resolve; /* 1 (default): re-solve flagged pixels in FP64; 0: keep
+                             the single-precision result */
+    int32_t reserved[4];
+} plk_params;
+
+typedef struct plk_ctx plk_ctx;
+typedef struct plk_state plk_state;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out is owned by the
+ * caller and released with plk_destroy.  Errors: EINVAL (null out, bad
+ * device), ENOMEM, ECUDA. */
+plk_status plk_create(plk_ctx **out, int device, void *cuda_stream);
+plk_status plk_destroy(plk_ctx *ctx);
+/* Switch the stream used by later calls. */
+plk_status plk_set_stream(plk_ctx *ctx, void *cuda_stream);
+/* Text of the last error on this context (static storage owned by ctx). */
+const char *plk_last_error(const plk_ctx *ctx);
+/* Fill *p with the defaults listed in plk_params. */
+plk_status plk_default_params(plk_params *p);
+/* Output grid of a window: *Ho = H / sy, *Wo = W / sx (host). */
+plk_status plk_output_shape(int H, int W, plk_window win, int *Ho, int *Wo);
+/* Mask words per output pixel: ceil(wy*wx / 64) (host). */
+int plk_mask_words(plk_window win);
+
+/* GLRT threshold (Sec. III-A), host only.  For n_eff samples per pixel the
+ * power ratio of two homogeneous pixels is F(2n, 2n) distributed, and the
+ * size-alpha GLRT accepts iff max/min <= c = F^{-1}_{2n,2n}(1 - alpha/2).
+ * Writes c to *c (host pointer).  EINVAL if alpha not in (0,1) or n_eff < 1. */
+plk_status plk_glrt_threshold(double alpha, int n_eff, double *c);
+
+/* ---------------------------------------------------------- hot-path calls */
+
+/* S1. Amplitude statistics (Sec. III-A, eqs. (merged-mean), (merged-variance)
+ * with equal weight per image).  For each pixel of slc [n][H][W]:
+ *   P = sum_t fl(fl(re^2) + fl(im^2)),  A = sum_t sqrt(...),  t ascending,
+ * single precision, no fused multiply-add (the sums decide mask bits).
+ * accumulate = 0: sum_pow = P (and sum_amp = A); accumulate = 1: sum_pow +=
+ * P (one float add), which merges a new group into the running statistics.
+ * sum_pow [H][W] float is required; sum_amp may be NULL.  n >= 1. */
+plk_status plk_amp_stats(plk_ctx *ctx, const plk_c64 *slc, int n, int H, int W,
+                         float *sum_pow, float *sum_amp, int accumulate);
+
+/* S2. SHP selection by GLRT (Sec. III-A).  sum_pow [H][W] holds the power
+ * sums over n_eff real images.  For output pixel p (centre as above) and
+ * window offset (dy, dx), bit (dy+hy)*wx + (dx+hx) of mask[p] is set iff the
+ * neighbour q is inside the image, P_p > 0, P_q > 0 and
+ *   max(P_p, P_q) <= fl(c * min(P_p, P_q)),  c = (float) plk_glrt_threshold.
+ * mask is [Ho][Wo][plk_mask_words(win)] uint64; count [Ho][Wo] uint16 gets the
+ * number of set bits (the paper's shp_counts layer; 0 marks no-data). */
+plk_status plk_shp_select(plk_ctx *ctx, const float *sum_pow, int n_eff, int H, int W,
+                          plk_window win, double alpha, uint64_t *mask, uint16_t *count);
+
+/* S3. Sample coherence (Sec. II-A, eq. (sample-coherence)).  For each output
+ * pixel, S_ik = sum over the set mask bits q of z_i(q) conj(z_k(q)), and
+ * C_ik = S_ik / sqrt(S_ii S_kk) (unit-power assumption of Sec. II-A), C_ii = 1,
+ * C_ik = 0 where S_ii or S_kk is 0; an empty mask gives NaN entries.
+ * slc [N][H][W]; mask as written by plk_shp_select for the same window;
+ * C_packed [Ho][Wo][N(N+1)/2], upper triangle by rows: entry (i, k), i <= k,
+ * at i*N - i*(i-1)/2 + (k - i).  Single-precision accumulation. */
+plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W,
+                                   plk_window win, const uint64_t *mask, plk_c64 *C_packed);
+
+/* S4-S6. EMI phase linking (Sec. III-B, eq. (emi-eigenvalue-problem)) with the
+ * reference of Sec. II-A and gamma_t of Sec. III-C, eq. (temporal-coherence).
+ * For each of npx packed coherences C_packed [npx][N(N+1)/2]:
+ *   G = (1-beta)|C| + beta I; v = eigenvector of the smallest eigenvalue of
+ *   G^{-1} o C by inverse iteration with shift mu; EVD fallback (largest
+ *   eigenvector of C) where the inversion of G fails;
+ *   phase[i][p] = arg(v_i conj(v_ref)) in (-pi, pi], phase[ref][p] = 0;
+ *   tcoh[p] = gamma_t over all N entries; lambda_min[p] = the eigenvalue
+ *   (NaN on EVD fallback); status[p] as PLK_PX_*.
+ * phase [N][npx] float; tcoh, lambda_min [npx] float (either may be NULL);
+ * status [npx] uint8 (required).  0 <= ref_idx < N.  params NULL = defaults. */
+plk_status plk_phase_link(plk_ctx *ctx, const plk_c64 *C_packed, int N, int64_t npx,
+                          int ref_idx, const plk_params *params, float *phase, float *tcoh,
+                          float *lambda_min, uint8_t *status);
+
+/* S7. Compressed SLC (Sec. II-B): kappa(y, x) = sum over the real entries
+ * i in [first_real, N) of exp(-j phase_i(cell)) z_i(y, x), a plain sum, where
+ * cell = (min(y/sy, Ho-1), min(x/sx, Wo-1)) is the output pixel whose
+ * decimation block holds (y, x).  A cell with NaN phases gives kappa = 0.
+ * slc [N][H][W]; phase [N][Ho][Wo] (only rows >= first_real are read);
+ * kappa [H][W].  0 <= first_real < N. */
+plk_status plk_compress(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real, int H, int W,
+                        plk_window win, const float *phase, plk_c64 *kappa);
+
+/* ------------------------------------------------- sequential state (S8) */
+
+/* State of one sequential chain (Sec. II-B): the ring of the K_max most recent
+ * compressed SLCs, the merged power/amplitude sums and the image count.
+ * Allocates every buffer a step needs for images of H x W, window win and at
+ * most M_max new SLCs per step (K_max + M_max <= PLK_MAX_N), so that
+ * plk_ministack_step allocates nothing.  Owned by the caller; release with
+ * plk_state_destroy.  Errors: EINVAL, ENOMEM. */
+plk_status plk_state_create(plk_ctx *ctx, int H, int W, plk_window win, int K_max, int M_max,
+                            plk_state **out);
+plk_status plk_state_destroy(plk_state *st);
+/* Host-side counters: compressed SLCs held, real images merged, steps run. */
+plk_status plk_state_info(const plk_state *st, int *K_used, int *n_eff, int *steps);
+/* Device pointer to compressed SLC i of the ring (0 = oldest), [H][W]. */
+plk_status plk_state_kappa(const plk_state *st, int i, const plk_c64 **kappa);
+/* Device pointers to the merged sums [H][W] (sum_amp may be NULL). */
+plk_status plk_state_sums(const plk_state *st, const float **sum_pow, const float **sum_amp);
+/* Checkpoint: write/read the ring, sums and counters to/from a file (host
+ * path).  load creates a new state (as plk_state_create) on ctx's device. */
+plk_status plk_state_save(plk_ctx *ctx, const plk_state *st, const char *path);
+plk_status plk_state_load(plk_ctx *ctx, const char *path, int M_max, plk_state **out);
+
+/* S1-S8. One step of the always-first mini-stack scheme (Sec. II-B items
+ * 1-3; NRT workflow steps 1-4 of Sec. III-G): merge the statistics of the M
+ * new SLCs new_slc [M][H][W] into st; GLRT SHP selection with n_eff = all
+ * real images so far; mini-stack = [ring oldest..newest, new SLCs]; coherence;
+ * EMI with reference = the newest compressed SLC (or the first new SLC on the
+ * first step); gamma_t; compress the new SLCs into a new kappa and push it
+ * (dropping the oldest beyond K_max).  Outputs for the real dates only:
+ * phase [M][Ho][Wo] relative to the first date of the archive, tcoh [Ho][Wo],
+ * status [Ho][Wo]; shp_count [Ho][Wo] may be NULL.  1 <= M <= M_max and
+ * M + (compressed SLCs held) >= 2.  params NULL = defaults. */
+plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
+                              const plk_params *params, float *phase, float *tcoh,
+                              uint8_t *status, uint16_t *shp_count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLK_H_ */

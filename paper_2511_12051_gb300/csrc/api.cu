@@ -1,0 +1,534 @@
+// C ABI of libplk (include/plk.h): argument checking, context and state
+// ownership, and the launch sequence of each call.  Host code only.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "plk_internal.cuh"
+
+struct plk_ctx {
+    int device;
+    cudaStream_t stream;
+    char err[512];
+};
+
+struct plk_state {
+    int device;
+    int H, W;
+    plk_window win;
+    int K_max, M_max;
+    int K_used, n_eff, steps, head;
+    float2 **ring;       // K_max planes [H][W]
+    float *sum_pow;      // [H][W]
+    float *sum_amp;      // [H][W]
+    uint64_t *mask;      // [Ho][Wo][nwords]
+    uint16_t *count;     // [Ho][Wo]
+    float2 *C;           // [Ho*Wo][ntri(K_max+M_max)]
+    float *phase_all;    // [K_max+M_max][Ho][Wo]
+};
+
+namespace {
+
+thread_local char g_noctx_err[512];
+
+plk_status fail(plk_ctx *ctx, plk_status st, const char *fmt, ...) {
+    char *dst = ctx ? ctx->err : g_noctx_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+plk_status cuda_fail(plk_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, PLK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Make ctx's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool window_ok(plk_window w) {
+    return w.wy >= 1 && w.wx >= 1 && (w.wy & 1) && (w.wx & 1) && w.sy >= 1 && w.sx >= 1 &&
+           (long long)w.wy * w.wx <= PLK_MAX_WINDOW;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Regularised incomplete beta I_x(a, b) by the continued fraction for the
+// incomplete beta function (evaluated with the modified Lentz method), with
+// the prefactor x^a (1-x)^b / (a B(a, b)) from log-gamma.  Used for x below
+// the mean a/(a+b) only (the GLRT solves in x <= 1/2 with a = b).
+double inc_beta_cf(double a, double b, double x) {
+    if (x <= 0.0) return 0.0;
+    const double lbeta = lgamma(a) + lgamma(b) - lgamma(a + b);
+    const double front = exp(a * log(x) + b * log1p(-x) - lbeta) / a;
+    const double tiny = 1e-300;
+    double f = 1.0, c = 1.0, d = 0.0;
+    for (int i = 0; i <= 4000; ++i) {
+        const int m = i / 2;
+        double num;
+        if (i == 0) num = 1.0;
+        else if (i % 2 == 0) num = (m * (b - m) * x) / ((a + 2.0 * m - 1.0) * (a + 2.0 * m));
+        else num = -((a + m) * (a + b + m) * x) / ((a + 2.0 * m) * (a + 2.0 * m + 1.0));
+        d = 1.0 + num * d;
+        if (fabs(d) < tiny) d = tiny;
+        d = 1.0 / d;
+        c = 1.0 + num / c;
+        if (fabs(c) < tiny) c = tiny;
+        const double cd = c * d;
+        f *= cd;
+        if (fabs(1.0 - cd) < 1e-16) break;
+    }
+    return front * (f - 1.0);
+}
+
+}  // namespace
+
+namespace plk {
+
+int device_sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+}  // namespace plk
+
+using plk::Geom;
+using plk::Planes;
+
+extern "C" {
+
+plk_status plk_default_params(plk_params *p) {
+    if (!p) return fail(nullptr, PLK_EINVAL, "plk_default_params: null params");
+    memset(p, 0, sizeof(*p));
+    p->alpha = 1e-3;
+    p->beta = 0.0f;
+    p->mu = 0.99f;
+    p->tol = 1e-6f;
+    p->max_iter = 50;
+    p->cond_max = 1e4f;
+    p->fp64_resolve = 1;
+    return PLK_OK;
+}
+
+plk_status plk_output_shape(int H, int W, plk_window win, int *Ho, int *Wo) {
+    if (!Ho || !Wo || H < 1 || W < 1 || !window_ok(win)) return fail(nullptr, PLK_EINVAL, "plk_output_shape: bad argument");
+    *Ho = H / win.sy;
+    *Wo = W / win.sx;
+    return PLK_OK;
+}
+
+int plk_mask_words(plk_window win) { return (win.wy * win.wx + 63) / 64; }
+
+plk_status plk_glrt_threshold(double alpha, int n_eff, double *c) {
+    if (!c || !(alpha > 0.0 && alpha < 1.0) || n_eff < 1)
+        return fail(nullptr, PLK_EINVAL, "plk_glrt_threshold: need 0 < alpha < 1, n_eff >= 1");
+    // X = P_p / (P_p + P_q) ~ Beta(n, n); find x with I_x(n, n) = alpha / 2.
+    const double a = n_eff, target = 0.5 * alpha;
+    double lo = 0.0, hi = 0.5;
+    for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (inc_beta_cf(a, a, mid) < target) lo = mid;
+        else hi = mid;
+    }
+    const double x = 0.5 * (lo + hi);
+    *c = (1.0 - x) / x;
+    return PLK_OK;
+}
+
+plk_status plk_create(plk_ctx **out, int device, void *cuda_stream) {
+    if (!out) return fail(nullptr, PLK_EINVAL, "plk_create: null out");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, PLK_ECUDA, "plk_create: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(nullptr, PLK_EINVAL, "plk_create: device %d of %d", device, ndev);
+    plk_ctx *ctx = new (std::nothrow) plk_ctx;
+    if (!ctx) return fail(nullptr, PLK_ENOMEM, "plk_create: out of host memory");
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->err[0] = 0;
+    *out = ctx;
+    return PLK_OK;
+}
+
+plk_status plk_destroy(plk_ctx *ctx) {
+    delete ctx;
+    return PLK_OK;
+}
+
+plk_status plk_set_stream(plk_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_set_stream: null ctx");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return PLK_OK;
+}
+
+const char *plk_last_error(const plk_ctx *ctx) { return ctx ? ctx->err : g_noctx_err; }
+
+plk_status plk_amp_stats(plk_ctx *ctx, const plk_c64 *slc, int n, int H, int W, float *sum_pow, float *sum_amp,
+                         int accumulate) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_amp_stats: null ctx");
+    if (!slc || !sum_pow || n < 1 || H < 1 || W < 1)
+        return fail(ctx, PLK_EINVAL, "plk_amp_stats: bad argument");
+    if (!aligned(slc, 8) || !aligned(sum_pow, 4) || (sum_amp && !aligned(sum_amp, 4)))
+        return fail(ctx, PLK_EINVAL, "plk_amp_stats: misaligned pointer");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(slc), n, (long long)H * W, sum_pow,
+                                          sum_amp, accumulate, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_amp_stats");
+    return PLK_OK;
+}
+
+plk_status plk_shp_select(plk_ctx *ctx, const float *sum_pow, int n_eff, int H, int W, plk_window win,
+                          double alpha, uint64_t *mask, uint16_t *count) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_shp_select: null ctx");
+    if (!sum_pow || H < 1 || W < 1 || !window_ok(win) || n_eff < 1 || !(alpha > 0 && alpha < 1))
+        return fail(ctx, PLK_EINVAL, "plk_shp_select: bad argument");
+    if ((long long)(H / win.sy) * (W / win.sx) > 0 && (!mask || !count))
+        return fail(ctx, PLK_EINVAL, "plk_shp_select: null output");
+    if (!aligned(sum_pow, 4) || !aligned(mask, 8) || !aligned(count, 2))
+        return fail(ctx, PLK_EINVAL, "plk_shp_select: misaligned pointer");
+    double c;
+    plk_glrt_threshold(alpha, n_eff, &c);
+    DeviceGuard dg(ctx->device);
+    const Geom g = plk::make_geom(H, W, win);
+    cudaError_t e = plk::launch_shp(sum_pow, g, (float)c, mask, count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_shp_select");
+    return PLK_OK;
+}
+
+plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W, plk_window win,
+                                   const uint64_t *mask, plk_c64 *C_packed) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_estimate_covariance: null ctx");
+    if (!slc || N < 2 || N > PLK_MAX_N || H < 1 || W < 1 || !window_ok(win))
+        return fail(ctx, PLK_EINVAL, "plk_estimate_covariance: bad argument");
+    if ((long long)(H / win.sy) * (W / win.sx) > 0 && (!mask || !C_packed))
+        return fail(ctx, PLK_EINVAL, "plk_estimate_covariance: null pointer");
+    if (!aligned(slc, 8) || !aligned(mask, 8) || !aligned(C_packed, 8))
+        return fail(ctx, PLK_EINVAL, "plk_estimate_covariance: misaligned pointer");
+    DeviceGuard dg(ctx->device);
+    const Geom g = plk::make_geom(H, W, win);
+    Planes z{};
+    for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
+    cudaError_t e = plk::launch_covariance(z, N, g, mask, reinterpret_cast<float2 *>(C_packed), ctx->stream);
+    if (e == cudaErrorInvalidConfiguration)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_estimate_covariance: window %dx%d with N=%d exceeds shared memory",
+                    win.wy, win.wx, N);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_estimate_covariance");
+    return PLK_OK;
+}
+
+static plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha) {
+    plk_params p;
+    if (params) p = *params;
+    else plk_default_params(&p);
+    if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
+        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0))
+        return fail(ctx, PLK_EINVAL, "bad plk_params");
+    out->beta = p.beta;
+    out->mu = p.mu;
+    out->tol = p.tol;
+    out->cond_max = p.cond_max;
+    out->max_iter = p.max_iter;
+    out->fp64_resolve = p.fp64_resolve ? 1 : 0;
+    if (alpha) *alpha = p.alpha;
+    return PLK_OK;
+}
+
+plk_status plk_phase_link(plk_ctx *ctx, const plk_c64 *C_packed, int N, int64_t npx, int ref_idx,
+                          const plk_params *params, float *phase, float *tcoh, float *lambda_min,
+                          uint8_t *status) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_phase_link: null ctx");
+    if (N < 2 || N > PLK_MAX_N || npx < 0 || ref_idx < 0 || ref_idx >= N)
+        return fail(ctx, PLK_EINVAL, "plk_phase_link: bad argument");
+    if (npx > 0 && (!C_packed || !phase || !status)) return fail(ctx, PLK_EINVAL, "plk_phase_link: null pointer");
+    if (!aligned(C_packed, 8) || !aligned(phase, 4) || (tcoh && !aligned(tcoh, 4)) ||
+        (lambda_min && !aligned(lambda_min, 4)))
+        return fail(ctx, PLK_EINVAL, "plk_phase_link: misaligned pointer");
+    plk::EmiParams prm;
+    plk_status st = resolve_params(ctx, params, &prm, nullptr);
+    if (st != PLK_OK) return st;
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = plk::launch_phase_link(reinterpret_cast<const float2 *>(C_packed), N, npx, ref_idx, prm, phase,
+                                           tcoh, lambda_min, status, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_phase_link");
+    return PLK_OK;
+}
+
+plk_status plk_compress(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real, int H, int W, plk_window win,
+                        const float *phase, plk_c64 *kappa) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_compress: null ctx");
+    if (!slc || !phase || !kappa || N < 1 || N > PLK_MAX_N || first_real < 0 || first_real >= N || H < 1 ||
+        W < 1 || !window_ok(win))
+        return fail(ctx, PLK_EINVAL, "plk_compress: bad argument");
+    if (!aligned(slc, 8) || !aligned(phase, 4) || !aligned(kappa, 8))
+        return fail(ctx, PLK_EINVAL, "plk_compress: misaligned pointer");
+    DeviceGuard dg(ctx->device);
+    const Geom g = plk::make_geom(H, W, win);
+    Planes z{};
+    for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
+    cudaError_t e =
+        plk::launch_compress(z, N, first_real, g, phase, reinterpret_cast<float2 *>(kappa), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_compress");
+    return PLK_OK;
+}
+
+// ------------------------------------------------------------------- state
+
+static void state_free(plk_state *st) {
+    if (!st) return;
+    if (st->ring) {
+        for (int i = 0; i < st->K_max; ++i) cudaFree(st->ring[i]);
+        free(st->ring);
+    }
+    cudaFree(st->sum_pow);
+    cudaFree(st->sum_amp);
+    cudaFree(st->mask);
+    cudaFree(st->count);
+    cudaFree(st->C);
+    cudaFree(st->phase_all);
+    delete st;
+}
+
+plk_status plk_state_create(plk_ctx *ctx, int H, int W, plk_window win, int K_max, int M_max, plk_state **out) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_state_create: null ctx");
+    if (!out || H < 1 || W < 1 || !window_ok(win) || K_max < 0 || M_max < 1 || K_max + M_max > PLK_MAX_N ||
+        K_max + M_max < 2)
+        return fail(ctx, PLK_EINVAL, "plk_state_create: bad argument");
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    plk_state *st = new (std::nothrow) plk_state;
+    if (!st) return fail(ctx, PLK_ENOMEM, "plk_state_create: host");
+    memset(st, 0, sizeof(*st));
+    st->device = ctx->device;
+    st->H = H;
+    st->W = W;
+    st->win = win;
+    st->K_max = K_max;
+    st->M_max = M_max;
+    const Geom g = plk::make_geom(H, W, win);
+    const long long npix = (long long)H * W, nout = (long long)g.Ho * g.Wo;
+    const int Nmax = K_max + M_max;
+    bool ok = true;
+    st->ring = (float2 **)calloc(K_max > 0 ? K_max : 1, sizeof(float2 *));
+    ok = ok && st->ring;
+    for (int i = 0; ok && i < K_max; ++i) ok = cudaMalloc(&st->ring[i], npix * sizeof(float2)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->sum_pow, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->sum_amp, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->mask, (nout > 0 ? nout : 1) * g.nwords * sizeof(uint64_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->count, (nout > 0 ? nout : 1) * sizeof(uint16_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->C, (nout > 0 ? nout : 1) * plk::ntri(Nmax) * sizeof(float2)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->phase_all, (nout > 0 ? nout : 1) * Nmax * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(st->sum_pow, 0, npix * sizeof(float), ctx->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(st->sum_amp, 0, npix * sizeof(float), ctx->stream) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        state_free(st);
+        return fail(ctx, PLK_ENOMEM, "plk_state_create: device allocation failed");
+    }
+    *out = st;
+    return PLK_OK;
+}
+
+plk_status plk_state_destroy(plk_state *st) {
+    if (!st) return PLK_OK;
+    DeviceGuard dg(st->device);
+    state_free(st);
+    return PLK_OK;
+}
+
+plk_status plk_state_info(const plk_state *st, int *K_used, int *n_eff, int *steps) {
+    if (!st) return fail(nullptr, PLK_EINVAL, "plk_state_info: null state");
+    if (K_used) *K_used = st->K_used;
+    if (n_eff) *n_eff = st->n_eff;
+    if (steps) *steps = st->steps;
+    return PLK_OK;
+}
+
+plk_status plk_state_kappa(const plk_state *st, int i, const plk_c64 **kappa) {
+    if (!st || !kappa || i < 0 || i >= st->K_used) return fail(nullptr, PLK_EINVAL, "plk_state_kappa: bad argument");
+    *kappa = reinterpret_cast<const plk_c64 *>(st->ring[(st->head + i) % st->K_max]);
+    return PLK_OK;
+}
+
+plk_status plk_state_sums(const plk_state *st, const float **sum_pow, const float **sum_amp) {
+    if (!st) return fail(nullptr, PLK_EINVAL, "plk_state_sums: null state");
+    if (sum_pow) *sum_pow = st->sum_pow;
+    if (sum_amp) *sum_amp = st->sum_amp;
+    return PLK_OK;
+}
+
+static const char kMagic[8] = {'P', 'L', 'K', 'S', 'T', 'A', 'T', '1'};
+
+plk_status plk_state_save(plk_ctx *ctx, const plk_state *st, const char *path) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_state_save: null ctx");
+    if (!st || !path) return fail(ctx, PLK_EINVAL, "plk_state_save: bad argument");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_state_save");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(ctx, PLK_EINVAL, "plk_state_save: cannot open %s", path);
+    const long long npix = (long long)st->H * st->W;
+    int32_t hdr[10] = {st->H, st->W, st->win.wy, st->win.wx, st->win.sy, st->win.sx,
+                       st->K_max, st->K_used, st->n_eff, st->steps};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1;
+    void *host = malloc(npix * sizeof(float2));
+    ok = ok && host;
+    for (int i = 0; ok && i < st->K_used; ++i) {
+        ok = cudaMemcpy(host, st->ring[(st->head + i) % st->K_max], npix * sizeof(float2), cudaMemcpyDeviceToHost) ==
+                 cudaSuccess &&
+             fwrite(host, sizeof(float2), npix, f) == (size_t)npix;
+    }
+    ok = ok && cudaMemcpy(host, st->sum_pow, npix * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess &&
+         fwrite(host, sizeof(float), npix, f) == (size_t)npix;
+    ok = ok && cudaMemcpy(host, st->sum_amp, npix * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess &&
+         fwrite(host, sizeof(float), npix, f) == (size_t)npix;
+    free(host);
+    if (fclose(f) != 0) ok = false;
+    if (!ok) return fail(ctx, PLK_ECUDA, "plk_state_save: write failed (%s)", path);
+    return PLK_OK;
+}
+
+plk_status plk_state_load(plk_ctx *ctx, const char *path, int M_max, plk_state **out) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_state_load: null ctx");
+    if (!path || !out) return fail(ctx, PLK_EINVAL, "plk_state_load: bad argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(ctx, PLK_EINVAL, "plk_state_load: cannot open %s", path);
+    char magic[8];
+    int32_t hdr[10];
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, sizeof(hdr), 1, f) != 1) {
+        fclose(f);
+        return fail(ctx, PLK_EINVAL, "plk_state_load: not a state file: %s", path);
+    }
+    plk_window win{hdr[2], hdr[3], hdr[4], hdr[5]};
+    plk_state *st = nullptr;
+    plk_status s = plk_state_create(ctx, hdr[0], hdr[1], win, hdr[6], M_max, &st);
+    if (s != PLK_OK) {
+        fclose(f);
+        return s;
+    }
+    if (hdr[7] < 0 || hdr[7] > st->K_max) {
+        fclose(f);
+        plk_state_destroy(st);
+        return fail(ctx, PLK_EINVAL, "plk_state_load: corrupt header");
+    }
+    DeviceGuard dg(ctx->device);
+    const long long npix = (long long)st->H * st->W;
+    void *host = malloc(npix * sizeof(float2));
+    bool ok = host != nullptr && cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+    for (int i = 0; ok && i < hdr[7]; ++i)
+        ok = fread(host, sizeof(float2), npix, f) == (size_t)npix &&
+             cudaMemcpy(st->ring[i], host, npix * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && fread(host, sizeof(float), npix, f) == (size_t)npix &&
+         cudaMemcpy(st->sum_pow, host, npix * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && fread(host, sizeof(float), npix, f) == (size_t)npix &&
+         cudaMemcpy(st->sum_amp, host, npix * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    free(host);
+    fclose(f);
+    if (!ok) {
+        plk_state_destroy(st);
+        return fail(ctx, PLK_EINVAL, "plk_state_load: truncated file %s", path);
+    }
+    st->K_used = hdr[7];
+    st->n_eff = hdr[8];
+    st->steps = hdr[9];
+    st->head = 0;
+    *out = st;
+    return PLK_OK;
+}
+
+plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M, const plk_params *params,
+                              float *phase, float *tcoh, uint8_t *status, uint16_t *shp_count) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_ministack_step: null ctx");
+    if (!st || !new_slc || M < 1 || M > st->M_max || st->K_used + M < 2)
+        return fail(ctx, PLK_EINVAL, "plk_ministack_step: bad argument");
+    const bool has_out = (long long)(st->H / st->win.sy) * (st->W / st->win.sx) > 0;
+    if (has_out && (!phase || !tcoh || !status))
+        return fail(ctx, PLK_EINVAL, "plk_ministack_step: null output");
+    if (!aligned(new_slc, 8) || !aligned(phase, 4) || !aligned(tcoh, 4) || (shp_count && !aligned(shp_count, 2)))
+        return fail(ctx, PLK_EINVAL, "plk_ministack_step: misaligned pointer");
+    if (st->device != ctx->device) return fail(ctx, PLK_EINVAL, "plk_ministack_step: state on another device");
+    plk::EmiParams prm;
+    double alpha;
+    plk_status ps = resolve_params(ctx, params, &prm, &alpha);
+    if (ps != PLK_OK) return ps;
+    DeviceGuard dg(ctx->device);
+    const Geom g = plk::make_geom(st->H, st->W, st->win);
+    const long long npix = (long long)st->H * st->W, nout = (long long)g.Ho * g.Wo;
+    const int K = st->K_used, N = K + M;
+    cudaStream_t s = ctx->stream;
+
+    // S1: merge the new images into the running power sums.
+    Planes znew{};
+    for (int t = 0; t < M; ++t) znew.p[t] = reinterpret_cast<const float2 *>(new_slc) + (long long)t * npix;
+    cudaError_t e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(new_slc), M, npix, st->sum_pow,
+                                          st->sum_amp, 1, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: amp_stats");
+    const int n_eff = st->n_eff + M;
+
+    // S2: SHP masks on the merged statistics.
+    double c;
+    plk_glrt_threshold(alpha, n_eff, &c);
+    uint16_t *cnt = shp_count ? shp_count : st->count;
+    e = plk::launch_shp(st->sum_pow, g, (float)c, st->mask, cnt, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: shp");
+
+    // Mini-stack: compressed SLCs oldest..newest, then the new real SLCs.
+    Planes z{};
+    for (int i = 0; i < K; ++i) z.p[i] = st->ring[(st->head + i) % st->K_max];
+    for (int t = 0; t < M; ++t) z.p[K + t] = znew.p[t];
+
+    // S3-S6.
+    e = plk::launch_covariance(z, N, g, st->mask, st->C, s);
+    if (e == cudaErrorInvalidConfiguration)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: window with N=%d exceeds shared memory", N);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: covariance");
+    const int ref = K > 0 ? K - 1 : 0;
+    e = plk::launch_phase_link(st->C, N, nout, ref, prm, st->phase_all, tcoh, nullptr, status, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: phase_link");
+    if (nout > 0) {
+        e = cudaMemcpyAsync(phase, st->phase_all + (long long)K * nout, (size_t)M * nout * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: phase copy");
+    }
+
+    // S7-S8: compress the real SLCs and push kappa into the ring.
+    if (st->K_max > 0) {
+        int slot;
+        if (K < st->K_max) slot = (st->head + K) % st->K_max;
+        else slot = st->head;
+        e = plk::launch_compress(z, N, K, g, st->phase_all, st->ring[slot], s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: compress");
+        if (K < st->K_max) st->K_used = K + 1;
+        else st->head = (st->head + 1) % st->K_max;
+    }
+    st->n_eff = n_eff;
+    st->steps += 1;
+    return PLK_OK;
+}
+
+}  // extern "C"

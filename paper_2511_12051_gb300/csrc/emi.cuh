@@ -1,0 +1,296 @@
+// S4-S6 device routines: EMI phase linking (Sec. III-B, eq.
+// (emi-eigenvalue-problem)), the reference phase (Sec. II-A) and the temporal
+// coherence (Sec. III-C, eq. (temporal-coherence)) of one pixel.
+//
+// A pixel is served by a group of NP lanes (NP = 8, 16 or 32 >= N); lane r owns
+// row r of every N x N matrix, held in registers.  Padded rows/columns
+// (r >= N) carry the identity and are never touched by the elimination steps.
+// Row broadcasts go through a per-group shared-memory buffer read with
+// 16-byte loads (one wavefront serves the whole group); reductions are
+// xor-butterflies inside the group, which leave bit-identical sums in every
+// lane, so loop exits stay group-uniform.
+//
+//   G   = (1 - beta)|C| + beta I, inverted in place by Gauss-Jordan without
+//         pivoting (for symmetric positive definite G its pivots are the
+//         squared Cholesky pivots).
+//   B   = G^{-1} o C - mu I, inverted the same way in complex arithmetic.
+//   v   = lim x_{t+1} = B^{-1} x_t / |B^{-1} x_t| (inverse iteration with
+//         shift mu = 0.99, Sec. III-B), started from the phases of column 0
+//         of C.
+//   EVD fallback where G is not invertible: power iteration on C (largest
+//         eigenvector, Sec. III-B).
+#pragma once
+
+#include "cpx.cuh"
+#include "plk_internal.cuh"
+
+namespace plk {
+
+template <class T> struct Lim;
+template <> struct Lim<float> {
+    static constexpr float piv_flag = 1e-6f;  // G pivot below: hand the pixel to the FP64 path
+    static constexpr float piv_fail = 1e-6f;  // G pivot below: inversion failed (FP32-only mode)
+    static constexpr float tiny = 1e-30f;
+    static constexpr float big = 3.0e38f;
+};
+template <> struct Lim<double> {
+    static constexpr double piv_flag = 0.0;
+    static constexpr double piv_fail = 1e-12;  // the Cholesky pivot limit of the FP64 reference
+    static constexpr double tiny = 1e-300;
+    static constexpr double big = 1e300;
+};
+
+template <int NP, class T>
+__device__ __forceinline__ T group_sum(T v, unsigned gmask) {
+#pragma unroll
+    for (int off = NP / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(gmask, v, off);
+    return v;
+}
+template <int NP, class T>
+__device__ __forceinline__ T group_max(T v, unsigned gmask) {
+#pragma unroll
+    for (int off = NP / 2; off >= 1; off >>= 1) v = fmax(v, __shfl_xor_sync(gmask, v, off));
+    return v;
+}
+template <int NP, class T>
+__device__ __forceinline__ T group_min(T v, unsigned gmask) {
+#pragma unroll
+    for (int off = NP / 2; off >= 1; off >>= 1) v = fmin(v, __shfl_xor_sync(gmask, v, off));
+    return v;
+}
+
+// ---- scalar helpers over real T and complex cpx<T> -----------------------
+__device__ __forceinline__ float inv_s(float a) { return 1.0f / a; }
+__device__ __forceinline__ double inv_s(double a) { return 1.0 / a; }
+template <class T>
+__device__ __forceinline__ cpx<T> inv_s(cpx<T> a) {
+    const T d = T(1) / norm2(a);
+    return mk<T>(a.x * d, -a.y * d);
+}
+__device__ __forceinline__ float mul_s(float a, float b) { return a * b; }
+__device__ __forceinline__ double mul_s(double a, double b) { return a * b; }
+template <class T>
+__device__ __forceinline__ cpx<T> mul_s(cpx<T> a, cpx<T> b) { return a * b; }
+__device__ __forceinline__ float fms_s(float a, float b, float c) { return c - a * b; }
+__device__ __forceinline__ double fms_s(double a, double b, double c) { return c - a * b; }
+template <class T>
+__device__ __forceinline__ cpx<T> fms_s(cpx<T> a, cpx<T> b, cpx<T> c) { return cfms(a, b, c); }
+__device__ __forceinline__ float neg_s(float a) { return -a; }
+__device__ __forceinline__ double neg_s(double a) { return -a; }
+template <class T>
+__device__ __forceinline__ cpx<T> neg_s(cpx<T> a) { return mk<T>(-a.x, -a.y); }
+__device__ __forceinline__ float re_s(float a) { return a; }
+__device__ __forceinline__ double re_s(double a) { return a; }
+template <class T>
+__device__ __forceinline__ T re_s(cpx<T> a) { return a.x; }
+__device__ __forceinline__ float real_s(float, float v) { return v; }
+__device__ __forceinline__ double real_s(double, double v) { return v; }
+template <class T>
+__device__ __forceinline__ cpx<T> real_s(cpx<T>, T v) { return mk<T>(v, T(0)); }
+
+// In-place Gauss-Jordan inverse of the n x n leading block of a matrix whose
+// row r is a[] (lane r of the group).  Step k: lane k publishes row k divided
+// by the pivot, with entry k replaced by 1/pivot; every lane then eliminates
+// its column-k entry while streaming the published row in 16-byte chunks.
+// PD = true (the real G): pivots are expected positive; a pivot <= `tiny` is
+// replaced by `tiny`.  PD = false (complex B, possibly indefinite): only a
+// pivot of magnitude below `tiny` is replaced.  Returns, in every lane, the
+// smallest real pivot met (before replacement).
+template <int NP, class T, class S, bool PD>
+__device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigned gmask) {
+    constexpr int E = 16 / sizeof(S);
+    static_assert(NP % E == 0, "row must be a multiple of 16 bytes");
+    T minpiv = Lim<T>::big;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        if (k >= n) break;
+        if (r == k) {
+            S piv = a[k];
+            const T pr = re_s(piv);
+            minpiv = fmin(minpiv, pr);
+            if (PD) {
+                if (!(pr > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
+            } else {
+                if (!(abs_t(pr) > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
+            }
+            const S inv = inv_s(piv);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) buf[j] = (j == k) ? inv : mul_s(a[j], inv);
+        }
+        __syncwarp(gmask);
+        const S f = a[k];
+        const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+#pragma unroll
+        for (int q = 0; q < NP / E; ++q) {
+            const uint4 v = src[q];
+            S rk[E];
+            memcpy(rk, &v, 16);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = q * E + e;
+                const S upd = (j == k) ? neg_s(mul_s(f, rk[e])) : fms_s(f, rk[e], a[j]);
+                a[j] = (r == k) ? rk[e] : upd;
+            }
+        }
+        __syncwarp(gmask);
+    }
+    return group_min<NP, T>(minpiv, gmask);
+}
+
+// y = sum_j a[j] * v_j where v (one entry per lane) is published in buf.
+template <int NP, class T>
+__device__ __forceinline__ cpx<T> group_matvec(const cpx<T> (&a)[NP], cpx<T> v, cpx<T> *buf, int r,
+                                               unsigned gmask) {
+    constexpr int E = 16 / sizeof(cpx<T>);
+    buf[r] = v;
+    __syncwarp(gmask);
+    cpx<T> y = mk<T>(T(0), T(0));
+    const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+#pragma unroll
+    for (int q = 0; q < NP / E; ++q) {
+        const uint4 u = src[q];
+        cpx<T> xs[E];
+        memcpy(xs, &u, 16);
+#pragma unroll
+        for (int e = 0; e < E; ++e) y = cfma(a[q * E + e], xs[e], y);
+    }
+    __syncwarp(gmask);
+    return y;
+}
+
+struct PixelResult {
+    float phase;  // this lane's linked phase (row r)
+    float tcoh;
+    float lam;
+    int status;
+    bool flag;    // the single-precision solve asks for the FP64 re-solve
+};
+
+// Row source: `load(k)` returns C_rk (complex, unit diagonal) of this lane's
+// row for k < n; padded entries are produced by the caller of the loader.
+template <int NP, class T, class Loader>
+__device__ __forceinline__ void load_crow(cpx<T> (&c)[NP], const Loader &load, int r, int n) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        if (r < n && k < n) c[k] = load(k);
+        else c[k] = mk<T>((k == r) ? T(1) : T(0), T(0));
+    }
+}
+
+// Solve one pixel.  With T = float and prm.fp64_resolve, an ill-conditioned
+// pixel returns flag = true and no outputs (the caller re-solves it with
+// T = double from the same loader).
+template <int NP, class T, class Loader>
+__device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, const EmiParams &prm,
+                                 cpx<T> *cbuf, unsigned gmask, int glane0, bool is_fp64) {
+    PixelResult out;
+    out.flag = false;
+    T *rbuf = reinterpret_cast<T *>(cbuf);
+    const bool live = r < n;
+
+    cpx<T> a[NP];
+    load_crow<NP, T>(a, load, r, n);
+
+    // G = (1 - beta)|C| + beta I, and its inverse.
+    T g[NP];
+    T rs = 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        T m = sqrt_t(norm2(a[k]));
+        if (prm.beta != 0.f) m = (T(1) - T(prm.beta)) * m + ((k == r) ? T(prm.beta) : T(0));
+        g[k] = m;
+        rs += abs_t(m);
+    }
+    const T norm_g = group_max<NP, T>(live ? rs : T(0), gmask);
+    const T minpiv = gj_invert<NP, T, T, true>(g, rbuf, r, n, gmask);
+    T rsi = 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) rsi += abs_t(g[k]);
+    const T norm_gi = group_max<NP, T>(live ? rsi : T(0), gmask);
+    const T cond = norm_g * norm_gi;
+    const bool finite = isfinite(cond);
+
+    if (!is_fp64 && prm.fp64_resolve &&
+        (minpiv <= Lim<T>::piv_flag || !finite || cond > T(prm.cond_max))) {
+        out.flag = true;
+        return out;
+    }
+    const bool inv_failed = (minpiv <= Lim<T>::piv_fail) || !finite;
+
+    // Iteration matrix: B^{-1} = (G^{-1} o C - mu I)^{-1}; C itself on fallback.
+    if (!inv_failed) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            a[k] = mk<T>(g[k] * a[k].x, g[k] * a[k].y);
+            if (k == r) a[k].x -= T(prm.mu);
+        }
+        gj_invert<NP, T, cpx<T>, false>(a, cbuf, r, n, gmask);
+    }
+
+    // Start vector: phases of column 0 of C (the interferograms to entry 0).
+    cpx<T> x;
+    {
+        const cpx<T> c0 = (live ? load(0) : mk<T>(T(0), T(0)));
+        const T m2 = norm2(c0);
+        x = (m2 > T(0)) ? (rsqrt_t(m2) * c0) : mk<T>(T(1), T(0));
+        x = live ? (rsqrt_t(T(n)) * x) : mk<T>(T(0), T(0));
+    }
+    const T tol = is_fp64 ? T(1e-10) : T(prm.tol);
+    const T tol2 = tol * tol;
+    cpx<T> d = mk<T>(T(1), T(0));
+    bool conv = false;
+    for (int it = 0; it < prm.max_iter; ++it) {
+        cpx<T> y = group_matvec<NP, T>(a, x, cbuf, r, gmask);
+        if (!live) y = mk<T>(T(0), T(0));
+        const T s = group_sum<NP, T>(norm2(y), gmask);          // |y|^2
+        d.x = group_sum<NP, T>(x.x * y.x + x.y * y.y, gmask);  // x^H y
+        d.y = group_sum<NP, T>(x.x * y.y - x.y * y.x, gmask);
+        const T dm2 = norm2(d);
+        // Unit iterate with x's common phase: y conj(d) / (|d| |y|).
+        const T sc = (s > T(0) && dm2 > T(0)) ? rsqrt_t(s) * rsqrt_t(dm2) : T(0);
+        const cpx<T> yn = (sc > T(0)) ? sc * (y * conj(d)) : x;
+        const T dl = group_sum<NP, T>(norm2(yn - x), gmask);
+        x = yn;
+        if (dl <= tol2) {
+            conv = true;
+            break;
+        }
+    }
+    // x^H B^{-1} x = 1 / (lambda - mu) at convergence (EMI); x^H C x on fallback.
+    const T lam = T(prm.mu) + T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
+
+    // Reference (Sec. II-A): phihat_i = arg(v_i conj(v_ref)), phihat_ref = 0.
+    cpx<T> vr;
+    vr.x = __shfl_sync(gmask, x.x, glane0 + ref);
+    vr.y = __shfl_sync(gmask, x.y, glane0 + ref);
+    const cpx<T> w = x * conj(vr);
+    T ph = atan2_t(w.y, w.x);
+    if (r == ref || !live) ph = T(0);
+
+    // gamma_t = |sum_{i<k} (C_ik / |C_ik|) conj(zeta_i) zeta_k| / (n(n-1)/2),
+    // zeta = exp(j phihat); an exactly-zero C_ik counts as phase 0.
+    const T wm2 = norm2(w);
+    cpx<T> zeta = (wm2 > T(0)) ? (rsqrt_t(wm2) * w) : mk<T>(T(1), T(0));
+    if (r == ref) zeta = mk<T>(T(1), T(0));
+    load_crow<NP, T>(a, load, r, n);
+    cpx<T> u[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const T m2 = norm2(a[k]);
+        const cpx<T> uk = (m2 > T(0)) ? (rsqrt_t(m2) * a[k]) : mk<T>(T(1), T(0));
+        u[k] = (k > r && k < n) ? uk : mk<T>(T(0), T(0));
+    }
+    const cpx<T> rowsum = group_matvec<NP, T>(u, zeta, cbuf, r, gmask);
+    const cpx<T> term = live ? (conj(zeta) * rowsum) : mk<T>(T(0), T(0));
+    const T sx = group_sum<NP, T>(term.x, gmask);
+    const T sy = group_sum<NP, T>(term.y, gmask);
+    const T tcoh = sqrt_t(sx * sx + sy * sy) / (T(0.5) * T(n) * T(n - 1));
+
+    out.phase = (float)ph;
+    out.tcoh = (float)tcoh;
+    out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
+    out.status = inv_failed ? PLK_PX_EVD : (!conv ? PLK_PX_NOCONV : (is_fp64 ? PLK_PX_EMI_FP64 : PLK_PX_EMI));
+    return out;
+}
+
+}  // namespace plk

@@ -1,0 +1,98 @@
+// S1 amplitude statistics and S2 GLRT SHP selection (Sec. III-A).
+//
+// Both kernels are HBM-streaming: one thread per pixel, coalesced 8-byte loads
+// across a warp, grid sized in multiples of the SM count.  The power sums and
+// the threshold product decide mask bits, so they use explicitly rounded
+// single-precision operations (__fmul_rn / __fadd_rn, never contracted into
+// an FMA) in one fixed order.
+#include "plk_internal.cuh"
+
+namespace plk {
+
+__global__ void __launch_bounds__(256) k_amp_stats(const float2 *__restrict__ z, int n, long long npix,
+                                                   float *__restrict__ sum_pow, float *__restrict__ sum_amp,
+                                                   int accumulate) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
+        float P = 0.0f, A = 0.0f;
+        for (int t = 0; t < n; ++t) {
+            const float2 v = __ldcs(z + (long long)t * npix + p);
+            const float q = __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
+            P = __fadd_rn(P, q);
+            A = __fadd_rn(A, __fsqrt_rn(q));
+        }
+        if (accumulate) {
+            sum_pow[p] = __fadd_rn(sum_pow[p], P);
+            if (sum_amp) sum_amp[p] = __fadd_rn(sum_amp[p], A);
+        } else {
+            sum_pow[p] = P;
+            if (sum_amp) sum_amp[p] = A;
+        }
+    }
+}
+
+// One thread per output pixel; the window's power sums come through L1.
+// Bit b = (dy+hy)*wx + (dx+hx); words are flushed as soon as they fill.
+__global__ void __launch_bounds__(256) k_shp(const float *__restrict__ P, const Geom g, float c,
+                                             uint64_t *__restrict__ mask, uint16_t *__restrict__ count) {
+    const long long nout = (long long)g.Ho * g.Wo;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < nout; o += stride) {
+        const int i = (int)(o / g.Wo), j = (int)(o % g.Wo);
+        const int cy = i * g.sy + g.sy / 2, cx = j * g.sx + g.sx / 2;
+        const float Pp = __ldg(P + (long long)cy * g.W + cx);
+        const bool valid = Pp > 0.0f;
+        uint64_t cur = 0;
+        int b = 0, w = 0, cnt = 0;
+        uint64_t *m = mask + o * g.nwords;
+        for (int dy = -g.hy; dy <= g.hy; ++dy) {
+            const int y = cy + dy;
+            const bool yin = (y >= 0) && (y < g.H);
+            for (int dx = -g.hx; dx <= g.hx; ++dx, ++b) {
+                const int x = cx + dx;
+                bool acc = false;
+                if (valid && yin && x >= 0 && x < g.W) {
+                    const float Pq = __ldg(P + (long long)y * g.W + x);
+                    const float hi = fmaxf(Pp, Pq), lo = fminf(Pp, Pq);
+                    acc = (Pq > 0.0f) && (hi <= __fmul_rn(c, lo));
+                }
+                if (acc) {
+                    cur |= 1ull << (b & 63);
+                    ++cnt;
+                }
+                if ((b & 63) == 63) {
+                    m[w++] = cur;
+                    cur = 0;
+                }
+            }
+        }
+        if (b & 63) m[w] = cur;
+        count[o] = (uint16_t)cnt;
+    }
+}
+
+static int grid_for(long long work, int block) {
+    const int sms = device_sm_count();
+    long long blocks = (work + block - 1) / block;
+    const long long cap = (long long)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+cudaError_t launch_amp_stats(const float2 *z, int n, long long npix, float *sum_pow, float *sum_amp,
+                             int accumulate, cudaStream_t s) {
+    if (npix == 0) return cudaSuccess;
+    k_amp_stats<<<grid_for(npix, 256), 256, 0, s>>>(z, n, npix, sum_pow, sum_amp, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *mask, uint16_t *count,
+                       cudaStream_t s) {
+    const long long nout = (long long)g.Ho * g.Wo;
+    if (nout == 0) return cudaSuccess;
+    k_shp<<<grid_for(nout, 256), 256, 0, s>>>(sum_pow, g, c, mask, count);
+    return cudaGetLastError();
+}
+
+}  // namespace plk

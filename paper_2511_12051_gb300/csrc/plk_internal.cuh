@@ -1,0 +1,64 @@
+// Internal declarations shared by the CUDA translation units of libplk.
+// Kernels are written for sm_103a (GB300).  Nothing here is part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plk.h"
+
+namespace plk {
+
+// Date planes of one mini-stack.  The planes of compressed SLCs (ring order)
+// and of the new real SLCs live in different buffers, so kernels receive one
+// base pointer per mini-stack entry, read from the parameter space.
+struct Planes {
+    const float2 *p[PLK_MAX_N];
+};
+
+struct Geom {
+    int H, W;        // input image
+    int wy, wx;      // window (odd)
+    int hy, hx;      // half window
+    int sy, sx;      // output strides
+    int Ho, Wo;      // output grid
+    int nwords;      // uint64 mask words per output pixel
+};
+
+inline Geom make_geom(int H, int W, plk_window w) {
+    Geom g;
+    g.H = H; g.W = W; g.wy = w.wy; g.wx = w.wx; g.hy = w.wy / 2; g.hx = w.wx / 2;
+    g.sy = w.sy; g.sx = w.sx; g.Ho = H / w.sy; g.Wo = W / w.sx;
+    g.nwords = (w.wy * w.wx + 63) / 64;
+    return g;
+}
+
+// Parameters of the phase-linking kernels, resolved on the host.
+struct EmiParams {
+    float beta, mu, tol, cond_max;
+    int max_iter;
+    int fp64_resolve;
+};
+
+__host__ __device__ inline long long ntri(int n) { return (long long)n * (n + 1) / 2; }
+__host__ __device__ inline int packed_index(int n, int i, int k) { return i * n - i * (i - 1) / 2 + (k - i); }
+
+// ---------------------------------------------------------------- launches
+// Each returns cudaGetLastError() after the launch.
+// z: n contiguous planes of npix samples.
+cudaError_t launch_amp_stats(const float2 *z, int n, long long npix, float *sum_pow, float *sum_amp,
+                             int accumulate, cudaStream_t s);
+cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *mask, uint16_t *count,
+                       cudaStream_t s);
+// Returns cudaErrorInvalidConfiguration if the window/N combination exceeds
+// shared memory even at a 1x1 output tile.
+cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
+                              cudaStream_t s);
+cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
+                              float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s);
+cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
+                            float2 *kappa, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace plk

@@ -1,0 +1,382 @@
+"""Python binding of libplk (include/plk.h): argument marshalling only.
+
+Every function takes CUDA torch tensors, checks dtype/device/contiguity, and
+calls the C entry point of the same name on the context's stream; all
+arithmetic runs in the library's CUDA kernels.  There is no CPU fallback: if
+libplk.so is missing or no GPU is present, calls raise.
+
+Layouts follow include/plk.h: stacks complex64 [N, H, W]; per-output-pixel
+arrays [Ho, Wo] with Ho = H // sy, Wo = W // sx; masks uint64 [Ho, Wo, words]
+(stored in an int64 tensor); packed coherences complex64 [Ho, Wo, N(N+1)/2].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libplk.so")
+
+PLK_MAX_N = 32
+PX_EMI, PX_EMI_FP64, PX_EVD, PX_NODATA, PX_NOCONV = 0, 1, 2, 3, 4
+_STATUS = {0: "PLK_OK", 1: "PLK_EINVAL", 2: "PLK_ENOMEM", 3: "PLK_ECUDA", 4: "PLK_ETIMEOUT", 5: "PLK_EUNSUPPORTED"}
+
+
+class PlkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Window(ctypes.Structure):
+    _fields_ = [("wy", ctypes.c_int32), ("wx", ctypes.c_int32), ("sy", ctypes.c_int32), ("sx", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_float), ("mu", ctypes.c_float),
+                ("tol", ctypes.c_float), ("max_iter", ctypes.c_int32), ("cond_max", ctypes.c_float),
+                ("fp64_resolve", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "plk_create": [ctypes.POINTER(_P), _I, _P],
+    "plk_destroy": [_P],
+    "plk_set_stream": [_P, _P],
+    "plk_default_params": [ctypes.POINTER(Params)],
+    "plk_output_shape": [_I, _I, Window, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "plk_glrt_threshold": [ctypes.c_double, _I, ctypes.POINTER(ctypes.c_double)],
+    "plk_amp_stats": [_P, _P, _I, _I, _I, _P, _P, _I],
+    "plk_shp_select": [_P, _P, _I, _I, _I, Window, ctypes.c_double, _P, _P],
+    "plk_estimate_covariance": [_P, _P, _I, _I, _I, Window, _P, _P],
+    "plk_phase_link": [_P, _P, _I, ctypes.c_int64, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
+    "plk_compress": [_P, _P, _I, _I, _I, _I, Window, _P, _P],
+    "plk_state_create": [_P, _I, _I, Window, _I, _I, ctypes.POINTER(_P)],
+    "plk_state_destroy": [_P],
+    "plk_state_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "plk_state_kappa": [_P, _I, ctypes.POINTER(_P)],
+    "plk_state_sums": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "plk_state_save": [_P, _P, ctypes.c_char_p],
+    "plk_state_load": [_P, ctypes.c_char_p, _I, ctypes.POINTER(_P)],
+    "plk_ministack_step": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
+}
+EXPORTS = sorted(list(_SIGS) + ["plk_last_error", "plk_mask_words"])
+
+
+def lib():
+    """Load libplk.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise PlkError(5, f"{LIB_PATH} is not built; run `python -m paper_2511_12051_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.plk_last_error.argtypes = [_P]
+            L.plk_last_error.restype = ctypes.c_char_p
+            L.plk_mask_words.argtypes = [Window]
+            L.plk_mask_words.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(code: int, ctx=None):
+    if code != 0:
+        msg = lib().plk_last_error(ctx).decode(errors="replace")
+        raise PlkError(code, msg)
+
+
+def window(w) -> Window:
+    if isinstance(w, Window):
+        return w
+    wy, wx, sy, sx = (int(v) for v in w)
+    return Window(wy, wx, sy, sx)
+
+
+def default_params(**over) -> Params:
+    p = Params()
+    _check(lib().plk_default_params(ctypes.byref(p)))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def glrt_threshold(alpha: float, n_eff: int) -> float:
+    c = ctypes.c_double()
+    _check(lib().plk_glrt_threshold(float(alpha), int(n_eff), ctypes.byref(c)))
+    return c.value
+
+
+def output_shape(H: int, W: int, win) -> tuple[int, int]:
+    w = window(win)
+    return H // w.sy, W // w.sx
+
+
+def mask_words(win) -> int:
+    return int(lib().plk_mask_words(window(win)))
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, name: str, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name}: must be a CUDA tensor (no CPU path)")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name}: on {t.device}, context on {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+
+
+class Context:
+    """plk_ctx bound to a CUDA device and stream (default: the current stream)."""
+
+    def __init__(self, device=None, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise PlkError(3, "no CUDA device available (libplk has no CPU path)")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        h = ctypes.c_void_p()
+        _check(lib().plk_create(ctypes.byref(h), dev.index, ctypes.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        _check(lib().plk_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().plk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- calls
+    def amp_stats(self, slc: torch.Tensor, sum_pow: torch.Tensor | None = None,
+                  sum_amp: torch.Tensor | None = None, accumulate: bool = False):
+        _need(slc, torch.complex64, "slc", self.device)
+        n, H, W = slc.shape
+        if sum_pow is None:
+            sum_pow = torch.empty((H, W), dtype=torch.float32, device=self.device)
+        _need(sum_pow, torch.float32, "sum_pow", self.device)
+        if sum_amp is not None:
+            _need(sum_amp, torch.float32, "sum_amp", self.device)
+        _check(lib().plk_amp_stats(self.h, _ptr(slc), n, H, W, _ptr(sum_pow), _ptr(sum_amp), int(accumulate)), self.h)
+        return sum_pow, sum_amp
+
+    def shp_select(self, sum_pow: torch.Tensor, n_eff: int, win, alpha: float = 1e-3,
+                   mask: torch.Tensor | None = None, count: torch.Tensor | None = None):
+        _need(sum_pow, torch.float32, "sum_pow", self.device)
+        H, W = sum_pow.shape
+        w = window(win)
+        Ho, Wo = output_shape(H, W, w)
+        nw = mask_words(w)
+        if mask is None:
+            mask = torch.empty((Ho, Wo, nw), dtype=torch.int64, device=self.device)
+        if count is None:
+            count = torch.empty((Ho, Wo), dtype=torch.int16, device=self.device)
+        _need(mask, torch.int64, "mask", self.device)
+        _need(count, torch.int16, "count", self.device)
+        _check(lib().plk_shp_select(self.h, _ptr(sum_pow), int(n_eff), H, W, w, float(alpha), _ptr(mask),
+                                    _ptr(count)), self.h)
+        return mask, count
+
+    def estimate_covariance(self, slc: torch.Tensor, win, mask: torch.Tensor, C: torch.Tensor | None = None):
+        _need(slc, torch.complex64, "slc", self.device)
+        _need(mask, torch.int64, "mask", self.device)
+        N, H, W = slc.shape
+        w = window(win)
+        Ho, Wo = output_shape(H, W, w)
+        if C is None:
+            C = torch.empty((Ho, Wo, N * (N + 1) // 2), dtype=torch.complex64, device=self.device)
+        _need(C, torch.complex64, "C", self.device)
+        _check(lib().plk_estimate_covariance(self.h, _ptr(slc), N, H, W, w, _ptr(mask), _ptr(C)), self.h)
+        return C
+
+    def phase_link(self, C: torch.Tensor, N: int, ref: int, params: Params | None = None,
+                   want_lambda: bool = True):
+        _need(C, torch.complex64, "C", self.device)
+        if C.shape[-1] != N * (N + 1) // 2:
+            raise ValueError("C: last dimension must be N(N+1)/2")
+        lead = tuple(C.shape[:-1])
+        npx = 1
+        for s in lead:
+            npx *= s
+        phase = torch.empty((N,) + lead, dtype=torch.float32, device=self.device)
+        tcoh = torch.empty(lead, dtype=torch.float32, device=self.device)
+        lam = torch.empty(lead, dtype=torch.float32, device=self.device) if want_lambda else None
+        status = torch.empty(lead, dtype=torch.uint8, device=self.device)
+        p = params if params is not None else default_params()
+        _check(lib().plk_phase_link(self.h, _ptr(C), N, npx, int(ref), ctypes.byref(p), _ptr(phase), _ptr(tcoh),
+                                    _ptr(lam), _ptr(status)), self.h)
+        return {"phase": phase, "tcoh": tcoh, "lam": lam, "status": status}
+
+    def compress(self, slc: torch.Tensor, first_real: int, win, phase: torch.Tensor,
+                 kappa: torch.Tensor | None = None):
+        _need(slc, torch.complex64, "slc", self.device)
+        _need(phase, torch.float32, "phase", self.device)
+        N, H, W = slc.shape
+        if kappa is None:
+            kappa = torch.empty((H, W), dtype=torch.complex64, device=self.device)
+        _need(kappa, torch.complex64, "kappa", self.device)
+        _check(lib().plk_compress(self.h, _ptr(slc), N, int(first_real), H, W, window(win), _ptr(phase),
+                                  _ptr(kappa)), self.h)
+        return kappa
+
+
+class State:
+    """plk_state: the sequential chain (kappa ring, merged sums, counters)."""
+
+    def __init__(self, ctx: Context, H: int, W: int, win, K_max: int, M_max: int, _handle=None):
+        self.ctx = ctx
+        self.H, self.W = H, W
+        self.win = window(win)
+        self.K_max, self.M_max = K_max, M_max
+        if _handle is None:
+            h = ctypes.c_void_p()
+            _check(lib().plk_state_create(ctx.h, H, W, self.win, K_max, M_max, ctypes.byref(h)), ctx.h)
+            self.h = h
+        else:
+            self.h = _handle
+        self.Ho, self.Wo = output_shape(H, W, self.win)
+
+    @classmethod
+    def load(cls, ctx: Context, path: str, M_max: int):
+        h = ctypes.c_void_p()
+        _check(lib().plk_state_load(ctx.h, os.fsencode(path), int(M_max), ctypes.byref(h)), ctx.h)
+        # read the geometry back from the file header
+        import struct
+        with open(path, "rb") as f:
+            f.read(8)
+            hdr = struct.unpack("<10i", f.read(40))
+        return cls(ctx, hdr[0], hdr[1], hdr[2:6], hdr[6], M_max, _handle=h)
+
+    def save(self, path: str):
+        _check(lib().plk_state_save(self.ctx.h, self.h, os.fsencode(path)), self.ctx.h)
+
+    def info(self) -> dict:
+        k, n, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().plk_state_info(self.h, ctypes.byref(k), ctypes.byref(n), ctypes.byref(s)))
+        return {"K_used": k.value, "n_eff": n.value, "steps": s.value}
+
+    def kappa_ptr(self, i: int) -> int:
+        p = ctypes.c_void_p()
+        _check(lib().plk_state_kappa(self.h, int(i), ctypes.byref(p)))
+        return p.value
+
+    def kappa(self, i: int) -> torch.Tensor:
+        """Copy of compressed SLC i of the ring (0 = oldest)."""
+        return _copy_from_ptr(self.kappa_ptr(i), (self.H, self.W), torch.complex64, self.ctx)
+
+    def sum_pow(self) -> torch.Tensor:
+        p, a = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().plk_state_sums(self.h, ctypes.byref(p), ctypes.byref(a)))
+        return _copy_from_ptr(p.value, (self.H, self.W), torch.float32, self.ctx)
+
+    def step(self, new_slc: torch.Tensor, params: Params | None = None, out: dict | None = None,
+             want_count: bool = True) -> dict:
+        _need(new_slc, torch.complex64, "new_slc", self.ctx.device)
+        M = new_slc.shape[0]
+        if tuple(new_slc.shape[1:]) != (self.H, self.W):
+            raise ValueError("new_slc: wrong image size")
+        dev = self.ctx.device
+        if out is None:
+            out = {
+                "phase": torch.empty((M, self.Ho, self.Wo), dtype=torch.float32, device=dev),
+                "tcoh": torch.empty((self.Ho, self.Wo), dtype=torch.float32, device=dev),
+                "status": torch.empty((self.Ho, self.Wo), dtype=torch.uint8, device=dev),
+                "count": torch.empty((self.Ho, self.Wo), dtype=torch.int16, device=dev) if want_count else None,
+            }
+        p = params if params is not None else default_params()
+        _check(lib().plk_ministack_step(self.ctx.h, self.h, _ptr(new_slc), M, ctypes.byref(p), _ptr(out["phase"]),
+                                        _ptr(out["tcoh"]), _ptr(out["status"]), _ptr(out.get("count"))),
+               self.ctx.h)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().plk_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevArray:
+    """Minimal __cuda_array_interface__ view of a library-owned device buffer."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 3, "strides": None}
+
+
+_TYPESTR = {torch.complex64: "<c8", torch.float32: "<f4"}
+
+
+def _copy_from_ptr(ptr: int, shape, dtype, ctx: Context) -> torch.Tensor:
+    """Copy of a library-owned device buffer into a new tensor (stream-ordered)."""
+    view = torch.as_tensor(_DevArray(ptr, shape, _TYPESTR[dtype]), device=ctx.device)
+    with torch.cuda.stream(ctx.stream):
+        return view.clone()
+
+
+_default_ctx: dict = {}
+
+
+def context(device=None) -> Context:
+    """Process-wide default context for `device` on its current stream."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    key = (dev.index, torch.cuda.current_stream(dev).cuda_stream)
+    if key not in _default_ctx:
+        _default_ctx[key] = Context(dev)
+    return _default_ctx[key]
+
+
+# Module-level functions with the ABI's names, on the default context.
+def amp_stats(slc, sum_pow=None, sum_amp=None, accumulate=False):
+    return context(slc.device).amp_stats(slc, sum_pow, sum_amp, accumulate)
+
+
+def shp_select(sum_pow, n_eff, win, alpha=1e-3):
+    return context(sum_pow.device).shp_select(sum_pow, n_eff, win, alpha)
+
+
+def estimate_covariance(slc, win, mask):
+    return context(slc.device).estimate_covariance(slc, win, mask)
+
+
+def phase_link(C, N, ref, params=None):
+    return context(C.device).phase_link(C, N, ref, params)
+
+
+def compress(slc, first_real, win, phase):
+    return context(slc.device).compress(slc, first_real, win, phase)
+
+
+def ministack_step(state: State, new_slc, params=None):
+    return state.step(new_slc, params)

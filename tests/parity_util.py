@@ -1,0 +1,32 @@
+"""Helpers shared by the GPU parity tests (comparison only, no method arithmetic)."""
+import numpy as np
+import torch
+
+PHASE_TOL = 1e-4   # rad, single precision vs the FP64 oracle
+TCOH_TOL = 1e-5
+
+
+def wrapped_diff(a, b):
+    return np.abs(np.angle(np.exp(1j * (np.asarray(a, np.float64) - np.asarray(b, np.float64)))))
+
+
+def to_np(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy()
+
+
+def mask_np(t: torch.Tensor) -> np.ndarray:
+    return to_np(t).view(np.uint64)
+
+
+def count_np(t: torch.Tensor) -> np.ndarray:
+    return to_np(t).view(np.uint16)
+
+
+def phase_report(gpu_phase, orc_phase, valid=None):
+    d = wrapped_diff(gpu_phase, orc_phase)
+    if valid is not None:
+        d = d[..., valid] if d.ndim > valid.ndim else d[valid]
+    d = d[np.isfinite(d)]
+    if d.size == 0:
+        return {"max": 0.0, "p99": 0.0, "n": 0}
+    return {"max": float(d.max()), "p99": float(np.percentile(d, 99)), "n": int(d.size)}

@@ -1,0 +1,238 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: SHP masks, counts and power sums bit-exact; linked phase within 1e-4 rad
+(wrapped); temporal coherence within 1e-5; coherence and compressed SLCs within
+single-precision accumulation error.  Sizes are small enough for the oracle to
+finish in seconds but span several CTA tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_12051_gb300 import synth
+from parity_util import PHASE_TOL, TCOH_TOL, count_np, mask_np, phase_report, to_np, wrapped_diff
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plk():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2511_12051_gb300 import build, plk as _plk
+    build.build()
+    return _plk
+
+
+@pytest.fixture(scope="module")
+def ctx(plk):
+    return plk.Context("cuda:0")
+
+
+def stack(cfg, **over):
+    spec = synth.config_spec(cfg, **over)
+    return synth.generate(spec), spec
+
+
+# ------------------------------------------------------------------ S1, S2
+
+@pytest.mark.parametrize("shape", [(10, 64, 96), (15, 37, 53), (3, 1, 1)])
+def test_amp_stats_bit_exact(ctx, shape):
+    n, H, W = shape
+    z, _ = stack(1, N=n, H=H, W=W, seed=7)
+    P, A = oracle.amp_stats(z.numpy())
+    zg = z.cuda()
+    Pg, Ag = ctx.amp_stats(zg, sum_amp=torch.empty((H, W), device="cuda"))
+    assert np.array_equal(to_np(Pg), P)
+    assert np.array_equal(to_np(Ag), A)
+    z2, _ = stack(0, N=4, H=H, W=W, seed=8)
+    oracle.amp_stats(z2.numpy(), P, A, accumulate=True)
+    ctx.amp_stats(z2.cuda(), Pg, Ag, accumulate=True)
+    assert np.array_equal(to_np(Pg), P)
+    assert np.array_equal(to_np(Ag), A)
+
+
+@pytest.mark.parametrize("win", [(5, 11, 1, 1), (5, 11, 3, 6), (19, 37, 3, 6), (3, 3, 2, 2), (1, 1, 1, 1)])
+def test_shp_select_bit_exact(ctx, win):
+    z, spec = stack(1, N=15, H=61, W=134, seed=3)  # 5% persistent scatterers
+    P, _ = oracle.amp_stats(z.numpy())
+    P[7, 9:20] = 0.0  # a no-data streak
+    c = oracle.glrt_threshold(1e-3, 15)
+    m_o, n_o = oracle.shp_select(P, win, np.float32(c))
+    m_g, n_g = ctx.shp_select(torch.from_numpy(P).cuda(), 15, win, 1e-3)
+    assert np.array_equal(mask_np(m_g), m_o)
+    assert np.array_equal(count_np(n_g), n_o)
+
+
+# -------------------------------------------------------------------- S3
+
+@pytest.mark.parametrize("cfg,N,win", [(0, 10, (5, 11, 1, 1)), (1, 15, (5, 11, 3, 6)), (0, 2, (3, 5, 1, 1)),
+                                       (0, 21, (5, 11, 3, 6)), (0, 32, (5, 11, 3, 6)), (0, 18, (19, 37, 3, 6))])
+def test_covariance_parity(ctx, cfg, N, win):
+    z, _ = stack(cfg, N=N, H=50, W=97, seed=11)
+    zn = z.numpy()
+    P, _ = oracle.amp_stats(zn)
+    m, cnt = oracle.shp_select(P, win, np.float32(oracle.glrt_threshold(1e-3, N)))
+    C_o = oracle.covariance(zn, win, m)
+    C_g = to_np(ctx.estimate_covariance(z.cuda(), win, torch.from_numpy(m.view(np.int64)).cuda()))
+    ok = cnt > 0
+    assert np.all(np.isnan(C_g[~ok].real))
+    err = np.abs(C_g[ok] - C_o[ok])
+    assert err.max() < 2e-5, err.max()
+
+
+# ------------------------------------------------------------------ S4-S6
+
+def oracle_C(cfg, N, H, W, win, seed, **over):
+    z, _ = stack(cfg, N=N, H=H, W=W, seed=seed, **over)
+    zn = z.numpy()
+    P, _ = oracle.amp_stats(zn)
+    m, cnt = oracle.shp_select(P, win, np.float32(oracle.glrt_threshold(1e-3, N)))
+    C = oracle.covariance(zn, win, m)
+    # Both sides link the same single-precision coherence.
+    return C.astype(np.complex64)
+
+
+@pytest.mark.parametrize("cfg,N,ref", [(0, 10, 0), (1, 15, 0), (0, 2, 1), (0, 5, 2), (0, 16, 15), (0, 18, 3),
+                                       (1, 21, 5), (0, 30, 0), (0, 32, 31)])
+def test_phase_link_parity(ctx, cfg, N, ref):
+    win = (5, 11, 3, 6) if cfg == 1 else (5, 11, 1, 1)
+    C32 = oracle_C(cfg, N, 40, 70, win, seed=21 + N)
+    o = oracle.phase_link(C32.astype(np.complex128), N, ref, cond=True)
+    g = ctx.phase_link(torch.from_numpy(C32).cuda(), N, ref)
+    ph_g, tc_g, st_g = to_np(g["phase"]), to_np(g["tcoh"]), to_np(g["status"])
+    live = o["status"] != 3
+    assert np.array_equal(st_g == 3, ~live)
+    # the eigenvector is unique only with a gap; exclude (and count) degenerate pixels
+    clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+    rep = phase_report(ph_g, o["phase"], clear)
+    assert rep["max"] <= PHASE_TOL, rep
+    assert np.all(ph_g[ref][live] == 0.0)
+    assert np.nanmax(np.abs(tc_g[live] - o["tcoh"][live])) <= TCOH_TOL
+    assert (clear.sum() >= 0.98 * live.sum())
+
+
+def test_phase_link_closed_forms(ctx):
+    # N=2: linked phase = interferogram phase, gamma_t = 1, lambda_min = 1.
+    rng = np.random.default_rng(5)
+    g = rng.uniform(0.05, 0.95, 1000)
+    th = rng.uniform(-np.pi, np.pi, 1000)
+    C = np.stack([np.ones(1000), g * np.exp(1j * th), np.ones(1000)], 1).astype(np.complex64)
+    out = ctx.phase_link(torch.from_numpy(C).cuda(), 2, 0)
+    d = wrapped_diff(to_np(out["phase"])[1], np.angle(np.conj(C[:, 1])))
+    assert d.max() < 1e-5
+    assert np.abs(to_np(out["tcoh"]) - 1).max() < 1e-6
+    assert np.abs(to_np(out["lam"]) - 1).max() < 1e-4
+
+
+# -------------------------------------------------------------------- S7
+
+@pytest.mark.parametrize("win,first_real", [((5, 11, 3, 6), 0), ((5, 11, 1, 1), 2), ((3, 5, 4, 7), 1)])
+def test_compress_parity(ctx, win, first_real):
+    N, H, W = 6, 45, 101
+    z, _ = stack(0, N=N, H=H, W=W, seed=31)
+    Ho, Wo = H // win[2], W // win[3]
+    rng = np.random.default_rng(1)
+    ph = rng.uniform(-np.pi, np.pi, (N, Ho, Wo)).astype(np.float32)
+    ph[:, 2, 3] = np.nan
+    k_o = oracle.compress(z.numpy(), first_real, win, ph.astype(np.float64))
+    k_g = to_np(ctx.compress(z.cuda(), first_real, win, torch.from_numpy(ph).cuda()))
+    scale = np.abs(z.numpy()[first_real:]).sum(0)
+    assert np.max(np.abs(k_g - k_o) / (scale + 1e-6)) < 2e-6
+
+
+# ------------------------------------------------------------- S1-S8 chain
+
+def run_chain(plk, ctx, z, window, M, K_max, n_dates):
+    H, W = z.shape[1:]
+    st = plk.State(ctx, H, W, window, K_max=K_max, M_max=M)
+    orc = oracle.OracleChain(H, W, window, K_max=K_max, alpha=1e-3)
+    zg = z.cuda()
+    res = []
+    for sl in synth.ministack_slices(n_dates, M):
+        g = st.step(zg[sl].contiguous())
+        o = orc.step(z[sl].numpy())
+        res.append((g, o))
+    return res, st, orc
+
+
+@pytest.mark.parametrize("case", ["cfg0", "cfg1", "cfg3"])
+def test_ministack_chain_parity(plk, ctx, case):
+    if case == "cfg0":
+        z, spec = stack(0, H=72, W=90)
+        window, M, K_max, nd = (5, 11, 1, 1), 10, 6, 10
+    elif case == "cfg1":
+        z, spec = stack(1, H=96, W=300)
+        window, M, K_max, nd = (5, 11, 3, 6), 15, 6, 15
+    else:
+        z, spec = stack(3, scale=0.05)  # 60 dates, 102 x 204, step patch inside
+        window, M, K_max, nd = (5, 11, 1, 1), 15, 3, 60
+    res, st, orc = run_chain(plk, ctx, z, window, M, K_max, nd)
+    for k, (g, o) in enumerate(res):
+        assert np.array_equal(count_np(g["count"]), o["count"]), k
+        live = o["status"] != 3
+        clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+        K = o["K_used"]
+        rep = phase_report(to_np(g["phase"]), o["phase"][K:], clear)
+        assert rep["max"] <= PHASE_TOL, (k, rep)
+        tc = np.abs(to_np(g["tcoh"]) - o["tcoh"])[live]
+        assert tc.max() <= TCOH_TOL, (k, tc.max())
+    info = st.info()
+    assert info["n_eff"] == nd and info["K_used"] == min(K_max, len(res))
+    # the ring holds the same compressed SLCs (single vs double precision)
+    for i in range(info["K_used"]):
+        kg = to_np(st.kappa(i))
+        ko = orc.ring[i]
+        assert np.max(np.abs(kg - ko)) <= 1e-4 * np.max(np.abs(ko))
+    assert np.array_equal(to_np(st.sum_pow()), orc.sum_pow)
+
+
+def test_chain_checkpoint_resume(plk, ctx, tmp_path):
+    z, _ = stack(3, scale=0.03)
+    window, M = (5, 11, 1, 1), 15
+    H, W = z.shape[1:]
+    zg = z.cuda()
+    a = plk.State(ctx, H, W, window, K_max=3, M_max=M)
+    outs_a = [a.step(zg[sl].contiguous()) for sl in synth.ministack_slices(60, M)]
+    b = plk.State(ctx, H, W, window, K_max=3, M_max=M)
+    for sl in synth.ministack_slices(60, M)[:2]:
+        b.step(zg[sl].contiguous())
+    path = str(tmp_path / "chain.plk")
+    b.save(path)
+    b.close()
+    c = plk.State.load(ctx, path, M_max=M)
+    outs_c = [c.step(zg[sl].contiguous()) for sl in synth.ministack_slices(60, M)[2:]]
+    for ga, gc in zip(outs_a[2:], outs_c):
+        assert torch.equal(ga["phase"], gc["phase"])
+        assert torch.equal(ga["tcoh"], gc["tcoh"])
+    assert c.info() == a.info() | {"steps": 4}
+
+
+# ------------------------------------------------------------------ edges
+
+def test_edge_cases(plk, ctx):
+    # Output grid empty (H < sy): nothing to do, no error.
+    z = torch.zeros((3, 2, 50), dtype=torch.complex64, device="cuda")
+    st = plk.State(ctx, 2, 50, (5, 11, 3, 6), K_max=2, M_max=3)
+    out = st.step(z)
+    assert out["phase"].shape == (3, 0, 8)
+    # An all-zero image is all no-data.
+    st2 = plk.State(ctx, 9, 20, (5, 11, 1, 1), K_max=2, M_max=3)
+    out = st2.step(torch.zeros((3, 9, 20), dtype=torch.complex64, device="cuda"))
+    assert torch.all(out["status"] == plk.PX_NODATA) and torch.all(torch.isnan(out["phase"]))
+    # A window larger than the image, and N = 2.
+    zz, _ = stack(0, N=2, H=3, W=4, seed=2)
+    st3 = plk.State(ctx, 3, 4, (5, 11, 1, 1), K_max=0, M_max=2)
+    g = st3.step(zz.cuda())
+    orc = oracle.OracleChain(3, 4, (5, 11, 1, 1), K_max=0)
+    o = orc.step(zz.numpy())
+    assert np.array_equal(count_np(g["count"]), o["count"])
+    assert wrapped_diff(to_np(g["phase"]), o["phase_real"]).max() < PHASE_TOL
+    # Bad arguments are rejected before any launch.
+    with pytest.raises(plk.PlkError):
+        plk.State(ctx, 10, 10, (4, 11, 1, 1), K_max=2, M_max=3)
+    with pytest.raises(plk.PlkError):
+        plk.State(ctx, 10, 10, (5, 11, 1, 1), K_max=20, M_max=15)
+    with pytest.raises(plk.PlkError):
+        ctx.phase_link(torch.zeros((4, 3), dtype=torch.complex64, device="cuda"), 2, 5)
