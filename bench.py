@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the sequential phase-linking hot path on one GB300 per rank.
+
+A step is one mini-stack through the whole path (amplitude statistics, GLRT SHP
+selection, coherence, EMI phase linking with reference and temporal coherence,
+compressed SLC), i.e. one plk_ministack_step on the burst-shaped workload:
+N = 15 complex64 SLCs of 4096 x 16384 pixels, 11 x 5 window, output strides
+6 x 3 (1365 x 2730 output pixels), synthetic exponential-decay coherence with
+tau ~ U(12, 120) days and 5% persistent scatterers.  The stack (8.05 GB) is far
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the baseline this build has; the paper's system is a CPU cloud pipeline with no
+GPU path) on a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-linked pixels/s (N=15, 11×5 window) and % of HBM/FP32 roofline"
+UNIT = "output px/s"
+WINDOW = (5, 11, 3, 6)  # wy, wx, sy, sx  ("11 x 5", strides 6 x 3)
+N_DATES = 15
+H_FULL, W_FULL = 4096, 16384
+WORKLOAD = "burst-shaped mini-stack: N=15 complex64 SLCs x 4096x16384 px, 11x5 window, output strides 6x3"
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            pass
+    return {}
+
+
+# FP32 SIMT peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop
+# (FMA) x 2.070 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def flops_covariance(N: int, looks_total: float) -> float:
+    """Algorithmic flops of the Hermitian sample covariance: 4 N^2 per look."""
+    return 4.0 * N * N * looks_total
+
+
+def flops_emi(N: int, npx: int) -> float:
+    """Algorithmic flops of EMI per pixel: inverse of |C| and a factorisation of
+    the shifted Hadamard product ((8/3) N^3 each), ten inverse-iteration steps
+    (8 N^2 each) and gamma_t (~10 N^2)."""
+    return npx * ((16.0 / 3.0) * N ** 3 + 90.0 * N * N)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_crop_run(z_np, window, alpha=1e-3):
+    """One pass of the FP64 oracle over a crop (test infrastructure: the CPU baseline)."""
+    import oracle
+    N, H, W = z_np.shape
+    ch = oracle.OracleChain(H, W, window, K_max=6, alpha=alpha)
+    t = time.perf_counter()
+    ch.step(z_np)
+    return time.perf_counter() - t, (H // window[2]) * (W // window[3])
+
+
+def cpu_crop(z_dev, rows: int, cols: int):
+    import numpy as np
+    c = z_dev[:, :rows, :cols].contiguous().cpu().numpy()
+    return np.ascontiguousarray(c)
+
+
+def size_cpu_sample(z_dev, target_s: float):
+    """Pick a crop of the workload whose oracle run takes about target_s."""
+    cols = 4096
+    pilot_rows = 24
+    dt, npx = oracle_crop_run(cpu_crop(z_dev, pilot_rows, cols), WINDOW)
+    rate = npx / max(dt, 1e-6)
+    want_px = rate * target_s
+    rows = int(want_px / (cols // WINDOW[3])) * WINDOW[2]
+    rows = max(WINDOW[2] * 4, min(H_FULL, rows))
+    return rows, cols, rate
+
+
+def run_reference(args, rank: int):
+    """FP64 CPU oracle on the machine's host cores, bounded crop per step."""
+    import oracle
+    import torch
+    from paper_2511_12051_gb300 import synth
+    if rank != 0:
+        return 0
+    spec = synth.config_spec(1)
+    # Only the crop is drawn: the generator draws row chunks in order, so the
+    # first rows of a smaller image equal the full image's first rows.
+    spec.H = 512
+    z = synth.generate(spec, device="cpu")
+    per_step_target = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    rows, cols, _ = size_cpu_sample(z, per_step_target)
+    rows = min(rows, spec.H - spec.H % WINDOW[2])
+    crop = cpu_crop(z, rows, cols)
+    for _ in range(args.warmup):
+        oracle_crop_run(crop, WINDOW)
+    ts = []
+    npx = 0
+    for _ in range(args.steps):
+        dt, npx = oracle_crop_run(crop, WINDOW)
+        ts.append(dt)
+    mean = sum(ts) / len(ts)
+    value = npx / mean
+    sample = f"{rows}x{cols} px crop of the workload ({npx} output px) per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="plk", choices=["plk", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--rows", type=int, default=H_FULL, help="image rows (smaller cases for profiling only)")
+    ap.add_argument("--cols", type=int, default=W_FULL, help="image columns (smaller cases for profiling only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2511_12051_gb300 import build, synth
+    build.build()
+    from paper_2511_12051_gb300 import plk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    # Each rank processes its own burst (weak scaling; no data-path collective).
+    spec = synth.config_spec(1, seed=1 + rank, H=args.rows, W=args.cols)
+    z = synth.generate(spec, device=dev)
+    stream = torch.cuda.Stream(dev)
+    ctx = plk.Context(dev, stream)
+    st = plk.State(ctx, spec.H, spec.W, WINDOW, K_max=6, M_max=N_DATES)
+    params = plk.default_params()
+    with torch.cuda.stream(stream):
+        out = st.step(z, params)  # allocates the output tensors once
+    torch.cuda.synchronize(dev)
+    Ho, Wo = st.Ho, st.Wo
+    npx = Ho * Wo
+
+    def one_step():
+        st.reset()
+        st.step(z, params, out=out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    torch.cuda.synchronize(dev)
+    looks_total = float(out["count"].view(torch.int16).to(torch.int32).sum().item())  # SHP looks, all pixels
+    status_hist = torch.bincount(out["status"].view(-1).to(torch.int64), minlength=5).tolist()
+
+    # ---------------------------------------------------------- timed region
+    clocks = ClockSampler(local)
+    ctx.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    kernels = ctx.profile_collect()
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = npx * world * args.steps / (ms_total / 1e3)
+    launches = sum(c for _, c in kernels.values())
+
+    # ------------------------------------------------------------- roofline
+    peaks = measured_peaks()
+    dom = max(kernels.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    dom_avg_s = dom_ms / dom_n / 1e3
+    if dom_name == "covariance":
+        work = flops_covariance(N_DATES, looks_total)
+        roof = {"bound": "alu", "achieved": work / dom_avg_s / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.070 GHz"}
+    elif dom_name.startswith("phase_link"):
+        work = flops_emi(N_DATES, npx)
+        roof = {"bound": "alu", "achieved": work / dom_avg_s / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.070 GHz"}
+    else:
+        nbytes = {"amp_stats": N_DATES * spec.H * spec.W * 8 + spec.H * spec.W * 8,
+                  "compress": N_DATES * spec.H * spec.W * 8 + spec.H * spec.W * 8,
+                  "shp_select": spec.H * spec.W * 4 + npx * 10}.get(dom_name, 0)
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": nbytes / dom_avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+    roof["kernel"] = dom_name
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None  # ncu DRAM bytes of the current kernel version: see profiles/
+    roof["avg_launch_ms"] = dom_ms / dom_n
+
+    # ------------------------------------------------------------------ e2e
+    e2e = None
+    if not args.no_e2e:
+        zh = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
+        zh.copy_(z)
+        oh = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items() if k != "count"}
+        bi = zh.numel() * zh.element_size()
+        bo = sum(v.numel() * v.element_size() for v in oh.values())
+
+        def e2e_step():
+            z.copy_(zh, non_blocking=True)
+            one_step()
+            for k, v in oh.items():
+                v.copy_(out[k], non_blocking=True)
+
+        with torch.cuda.stream(stream):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        ne = max(1, min(args.steps, 5))
+        with torch.cuda.stream(stream):
+            f0.record(stream)
+            for _ in range(ne):
+                e2e_step()
+            f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_e2e = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": npx * world * ne / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_e2e / ne}
+        del zh, oh
+
+    # ---------------------------------------------------------- CPU baseline
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rows, cols, _ = size_cpu_sample(z, args.cpu_seconds)
+        crop = cpu_crop(z, rows, cols)
+        dt, cnpx = oracle_crop_run(crop, WINDOW)
+        cpu = {"value": cnpx / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{rows}x{cols} px crop of the workload ({cnpx} output px), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if (spec.H, spec.W) == (H_FULL, W_FULL) else
+                       f"profiling case {spec.H}x{spec.W} (not the headline workload)", "N": N_DATES,
+                       "H": spec.H, "W": spec.W,
+                       "window_wy_wx_sy_sx": list(WINDOW), "output_px_per_gpu": npx,
+                       "l2": "inputs (8.05 GB per step) larger than L2; no flush",
+                       "parallelism": f"{world} independent bursts, one per GPU"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kernels.items()},
+            "pixel_status_hist": status_hist,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -70,14 +70,19 @@ typedef struct plk_params {
     float mu;          /* inverse-iteration shift (Sec. III-B); default 0.99 */
     float tol;         /* stop when the unit iterate moves less than tol (2-norm,
                           after removing a common phase); default 1e-6 */
-    int32_t max_iter;  /* inverse-iteration cap; default 50 */
-    float cond_max;    /* pixels whose 1-norm condition estimate of G exceeds
+    int32_t max_iter;  /* inverse-iteration cap, all shifts together; default 100 */
+    float cond_max;    /* pixels whose 1-norm condition number of G exceeds
                           cond_max, or whose single-precision inversion of G meets
-                          a pivot below 1e-6, are re-solved in double precision;
-                          default 1e4 */
+                          a pivot below 1e-6 without C being rank one, are
+                          re-solved in double precision; default 1e4 */
     int32_t fp64_resolve; /* 1 (default): re-solve flagged pixels in FP64; 0: keep
                              the single-precision result */
-    int32_t reserved[4];
+    float err_max;     /* pixels whose first-order single-precision error bound
+                          (condition of G times |G^-1| times eps over the
+                          eigengap seen by the iteration) exceeds err_max are
+                          re-solved in double precision; default 0.1 (the bound
+                          is loose: measured errors sit 1e3-1e4 below it) */
+    int32_t reserved[3];
 } plk_params;
 
 typedef struct plk_ctx plk_ctx;
@@ -101,6 +106,17 @@ plk_status plk_default_params(plk_params *p);
 plk_status plk_output_shape(int H, int W, plk_window win, int *Ho, int *Wo);
 /* Mask words per output pixel: ceil(wy*wx / 64) (host). */
 int plk_mask_words(plk_window win);
+
+/* Per-kernel timing (not part of the method).  While enabled, every kernel
+ * launch of a call is bracketed by CUDA events recorded on ctx's stream (up to
+ * 4096 launches between collections; enabling allocates the events).
+ * plk_profile_collect synchronizes the stream and aggregates the recorded
+ * launches by kernel stage name ("amp_stats", "shp_select", "covariance",
+ * "phase_link_fp32", "phase_link_fp64", "compress"); plk_profile_get returns
+ * stage i's name (static string), total milliseconds and launch count. */
+plk_status plk_profile_enable(plk_ctx *ctx, int enable);
+plk_status plk_profile_collect(plk_ctx *ctx, int *n_kernels);
+plk_status plk_profile_get(const plk_ctx *ctx, int i, const char **name, double *total_ms, int *launches);
 
 /* GLRT threshold (Sec. III-A), host only.  For n_eff samples per pixel the
  * power ratio of two homogeneous pixels is F(2n, 2n) distributed, and the
@@ -175,6 +191,9 @@ plk_status plk_compress(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real,
 plk_status plk_state_create(plk_ctx *ctx, int H, int W, plk_window win, int K_max, int M_max,
                             plk_state **out);
 plk_status plk_state_destroy(plk_state *st);
+/* Start a new chain on the same buffers: the next step is a first step (its
+ * statistics overwrite the sums; no compressed SLC is used).  Host only. */
+plk_status plk_state_reset(plk_state *st);
 /* Host-side counters: compressed SLCs held, real images merged, steps run. */
 plk_status plk_state_info(const plk_state *st, int *K_used, int *n_eff, int *steps);
 /* Device pointer to compressed SLC i of the ring (0 = oldest), [H][W]. */

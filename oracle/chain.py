@@ -39,7 +39,12 @@ def ministack(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, n_eff
 class OracleChain:
     """Sequential processing state: kappa ring, merged power sums, image count."""
 
-    def __init__(self, H: int, W: int, window, K_max: int, alpha: float = 1e-3, beta: float = 0.0):
+    def __init__(self, H: int, W: int, window, K_max: int, alpha: float = 1e-3, beta: float = 0.0,
+                 kappa_dtype=np.complex128):
+        # kappa_dtype=np.complex64 stores each compressed SLC rounded to the
+        # single-precision complex samples a stored SLC has (the form the GPU
+        # state keeps), so both sides can start a step from identical inputs.
+        self.kappa_dtype = kappa_dtype
         self.H, self.W = H, W
         self.window = tuple(window)
         self.K_max = K_max
@@ -60,7 +65,7 @@ class OracleChain:
         z = np.concatenate(parts, axis=0)
         ref = K - 1 if K > 0 else 0
         out = ministack(z, K, self.window, self.sum_pow, self.n, self.alpha, ref, self.beta, cond)
-        self.ring.append(out["kappa"])
+        self.ring.append(out["kappa"].astype(self.kappa_dtype).astype(np.complex128))
         if len(self.ring) > self.K_max:
             self.ring.pop(0)
         out["phase_real"] = out["phase"][K:]

@@ -49,18 +49,23 @@ def _digest() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "libplk.stamp")
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          out_dir: str | None = None) -> str:
+    """Compile and link; `out_dir` builds a variant (e.g. with extra -D flags)
+    next to, not over, the default library."""
+    build_dir = out_dir or BUILD
+    lib_path = os.path.join(build_dir, "libplk.so")
+    os.makedirs(build_dir, exist_ok=True)
+    stamp = os.path.join(build_dir, "libplk.stamp")
     dig = _digest() + ("" if not extra_flags else "|" + " ".join(extra_flags))
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
-        return LIB
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp) and open(stamp).read() == dig:
+        return lib_path
     cc = nvcc()
     flags = ARCH + NVCC_FLAGS + (extra_flags or [])
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -71,14 +76,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(dig)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -14,6 +14,12 @@ struct plk_ctx {
     int device;
     cudaStream_t stream;
     char err[512];
+    plk::Prof prof;
+    // aggregated by plk_profile_collect
+    int n_agg;
+    const char *agg_name[32];
+    double agg_ms[32];
+    int agg_count[32];
 };
 
 struct plk_state {
@@ -127,9 +133,10 @@ plk_status plk_default_params(plk_params *p) {
     p->beta = 0.0f;
     p->mu = 0.99f;
     p->tol = 1e-6f;
-    p->max_iter = 50;
+    p->max_iter = 100;
     p->cond_max = 1e4f;
     p->fp64_resolve = 1;
+    p->err_max = 0.1f;
     return PLK_OK;
 }
 
@@ -171,12 +178,75 @@ plk_status plk_create(plk_ctx **out, int device, void *cuda_stream) {
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->err[0] = 0;
+    ctx->n_agg = 0;
     *out = ctx;
     return PLK_OK;
 }
 
 plk_status plk_destroy(plk_ctx *ctx) {
+    if (!ctx) return PLK_OK;
+    if (ctx->prof.ev[0]) {
+        DeviceGuard dg(ctx->device);
+        for (int i = 0; i < 2 * plk::Prof::kMaxRecords; ++i) cudaEventDestroy(ctx->prof.ev[i]);
+    }
     delete ctx;
+    return PLK_OK;
+}
+
+plk_status plk_profile_enable(plk_ctx *ctx, int enable) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_profile_enable: null ctx");
+    DeviceGuard dg(ctx->device);
+    if (enable && !ctx->prof.ev[0]) {
+        for (int i = 0; i < 2 * plk::Prof::kMaxRecords; ++i)
+            if (cudaEventCreate(&ctx->prof.ev[i]) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, PLK_ENOMEM, "plk_profile_enable: cudaEventCreate failed");
+            }
+    }
+    ctx->prof.on = enable != 0;
+    ctx->prof.n = 0;
+    ctx->prof.overflow = false;
+    return PLK_OK;
+}
+
+plk_status plk_profile_collect(plk_ctx *ctx, int *n_kernels) {
+    if (!ctx || !n_kernels) return fail(ctx, PLK_EINVAL, "plk_profile_collect: bad argument");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_profile_collect");
+    ctx->n_agg = 0;
+    for (int i = 0; i < ctx->prof.n; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->prof.ev[2 * i], ctx->prof.ev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int j = 0;
+        while (j < ctx->n_agg && strcmp(ctx->agg_name[j], ctx->prof.name[i]) != 0) ++j;
+        if (j == ctx->n_agg) {
+            if (ctx->n_agg == 32) continue;
+            ctx->agg_name[j] = ctx->prof.name[i];
+            ctx->agg_ms[j] = 0.0;
+            ctx->agg_count[j] = 0;
+            ++ctx->n_agg;
+        }
+        ctx->agg_ms[j] += ms;
+        ctx->agg_count[j] += 1;
+    }
+    const bool over = ctx->prof.overflow;
+    ctx->prof.n = 0;
+    ctx->prof.overflow = false;
+    *n_kernels = ctx->n_agg;
+    if (over) return fail(ctx, PLK_EINVAL, "plk_profile_collect: more than %d launches recorded", plk::Prof::kMaxRecords);
+    return PLK_OK;
+}
+
+plk_status plk_profile_get(const plk_ctx *ctx, int i, const char **name, double *total_ms, int *launches) {
+    if (!ctx || i < 0 || i >= ctx->n_agg || !name || !total_ms || !launches)
+        return fail(nullptr, PLK_EINVAL, "plk_profile_get: bad argument");
+    *name = ctx->agg_name[i];
+    *total_ms = ctx->agg_ms[i];
+    *launches = ctx->agg_count[i];
     return PLK_OK;
 }
 
@@ -196,8 +266,10 @@ plk_status plk_amp_stats(plk_ctx *ctx, const plk_c64 *slc, int n, int H, int W, 
     if (!aligned(slc, 8) || !aligned(sum_pow, 4) || (sum_amp && !aligned(sum_amp, 4)))
         return fail(ctx, PLK_EINVAL, "plk_amp_stats: misaligned pointer");
     DeviceGuard dg(ctx->device);
+    ctx->prof.begin("amp_stats", ctx->stream);
     cudaError_t e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(slc), n, (long long)H * W, sum_pow,
                                           sum_amp, accumulate, ctx->stream);
+    ctx->prof.end(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_amp_stats");
     return PLK_OK;
 }
@@ -215,7 +287,9 @@ plk_status plk_shp_select(plk_ctx *ctx, const float *sum_pow, int n_eff, int H, 
     plk_glrt_threshold(alpha, n_eff, &c);
     DeviceGuard dg(ctx->device);
     const Geom g = plk::make_geom(H, W, win);
+    ctx->prof.begin("shp_select", ctx->stream);
     cudaError_t e = plk::launch_shp(sum_pow, g, (float)c, mask, count, ctx->stream);
+    ctx->prof.end(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_shp_select");
     return PLK_OK;
 }
@@ -233,7 +307,9 @@ plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int 
     const Geom g = plk::make_geom(H, W, win);
     Planes z{};
     for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
+    ctx->prof.begin("covariance", ctx->stream);
     cudaError_t e = plk::launch_covariance(z, N, g, mask, reinterpret_cast<float2 *>(C_packed), ctx->stream);
+    ctx->prof.end(ctx->stream);
     if (e == cudaErrorInvalidConfiguration)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_estimate_covariance: window %dx%d with N=%d exceeds shared memory",
                     win.wy, win.wx, N);
@@ -246,12 +322,13 @@ static plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::Em
     if (params) p = *params;
     else plk_default_params(&p);
     if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
-        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0))
+        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0))
         return fail(ctx, PLK_EINVAL, "bad plk_params");
     out->beta = p.beta;
     out->mu = p.mu;
     out->tol = p.tol;
     out->cond_max = p.cond_max;
+    out->err_max = p.err_max;
     out->max_iter = p.max_iter;
     out->fp64_resolve = p.fp64_resolve ? 1 : 0;
     if (alpha) *alpha = p.alpha;
@@ -273,7 +350,7 @@ plk_status plk_phase_link(plk_ctx *ctx, const plk_c64 *C_packed, int N, int64_t 
     if (st != PLK_OK) return st;
     DeviceGuard dg(ctx->device);
     cudaError_t e = plk::launch_phase_link(reinterpret_cast<const float2 *>(C_packed), N, npx, ref_idx, prm, phase,
-                                           tcoh, lambda_min, status, ctx->stream);
+                                           tcoh, lambda_min, status, ctx->stream, &ctx->prof);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_phase_link");
     return PLK_OK;
 }
@@ -290,8 +367,10 @@ plk_status plk_compress(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real,
     const Geom g = plk::make_geom(H, W, win);
     Planes z{};
     for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
+    ctx->prof.begin("compress", ctx->stream);
     cudaError_t e =
         plk::launch_compress(z, N, first_real, g, phase, reinterpret_cast<float2 *>(kappa), ctx->stream);
+    ctx->prof.end(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_compress");
     return PLK_OK;
 }
@@ -357,6 +436,15 @@ plk_status plk_state_destroy(plk_state *st) {
     if (!st) return PLK_OK;
     DeviceGuard dg(st->device);
     state_free(st);
+    return PLK_OK;
+}
+
+plk_status plk_state_reset(plk_state *st) {
+    if (!st) return fail(nullptr, PLK_EINVAL, "plk_state_reset: null state");
+    st->K_used = 0;
+    st->n_eff = 0;
+    st->steps = 0;
+    st->head = 0;
     return PLK_OK;
 }
 
@@ -485,8 +573,10 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     // S1: merge the new images into the running power sums.
     Planes znew{};
     for (int t = 0; t < M; ++t) znew.p[t] = reinterpret_cast<const float2 *>(new_slc) + (long long)t * npix;
+    ctx->prof.begin("amp_stats", s);
     cudaError_t e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(new_slc), M, npix, st->sum_pow,
-                                          st->sum_amp, 1, s);
+                                          st->sum_amp, st->n_eff > 0 ? 1 : 0, s);
+    ctx->prof.end(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: amp_stats");
     const int n_eff = st->n_eff + M;
 
@@ -494,7 +584,9 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     double c;
     plk_glrt_threshold(alpha, n_eff, &c);
     uint16_t *cnt = shp_count ? shp_count : st->count;
+    ctx->prof.begin("shp_select", s);
     e = plk::launch_shp(st->sum_pow, g, (float)c, st->mask, cnt, s);
+    ctx->prof.end(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: shp");
 
     // Mini-stack: compressed SLCs oldest..newest, then the new real SLCs.
@@ -503,12 +595,14 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     for (int t = 0; t < M; ++t) z.p[K + t] = znew.p[t];
 
     // S3-S6.
+    ctx->prof.begin("covariance", s);
     e = plk::launch_covariance(z, N, g, st->mask, st->C, s);
+    ctx->prof.end(s);
     if (e == cudaErrorInvalidConfiguration)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: window with N=%d exceeds shared memory", N);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: covariance");
     const int ref = K > 0 ? K - 1 : 0;
-    e = plk::launch_phase_link(st->C, N, nout, ref, prm, st->phase_all, tcoh, nullptr, status, s);
+    e = plk::launch_phase_link(st->C, N, nout, ref, prm, st->phase_all, tcoh, nullptr, status, s, &ctx->prof);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: phase_link");
     if (nout > 0) {
         e = cudaMemcpyAsync(phase, st->phase_all + (long long)K * nout, (size_t)M * nout * sizeof(float),
@@ -521,7 +615,9 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
         int slot;
         if (K < st->K_max) slot = (st->head + K) % st->K_max;
         else slot = st->head;
+        ctx->prof.begin("compress", s);
         e = plk::launch_compress(z, N, K, g, st->phase_all, st->ring[slot], s);
+        ctx->prof.end(s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: compress");
         if (K < st->K_max) st->K_used = K + 1;
         else st->head = (st->head + 1) % st->K_max;

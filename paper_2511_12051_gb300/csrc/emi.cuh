@@ -166,8 +166,14 @@ struct PixelResult {
     bool flag;    // the single-precision solve asks for the FP64 re-solve
 };
 
+constexpr int kPending = 0xFE;  // status of a pixel handed to the FP64 re-solve
+
+template <class T> struct Eps;
+template <> struct Eps<float> { static constexpr float v = 5.96e-8f; };
+template <> struct Eps<double> { static constexpr double v = 1.11e-16; };
+
 // Row source: `load(k)` returns C_rk (complex, unit diagonal) of this lane's
-// row for k < n; padded entries are produced by the caller of the loader.
+// row for k < n; padded entries are produced here.
 template <int NP, class T, class Loader>
 __device__ __forceinline__ void load_crow(cpx<T> (&c)[NP], const Loader &load, int r, int n) {
 #pragma unroll
@@ -177,9 +183,38 @@ __device__ __forceinline__ void load_crow(cpx<T> (&c)[NP], const Loader &load, i
     }
 }
 
-// Solve one pixel.  With T = float and prm.fp64_resolve, an ill-conditioned
-// pixel returns flag = true and no outputs (the caller re-solves it with
-// T = double from the same loader).
+// a <- (G^{-1} o C - mu I)^{-1}, from g = G^{-1} (this lane's row) and C.
+template <int NP, class T, class Loader>
+__device__ __forceinline__ void form_shift_inverse(cpx<T> (&a)[NP], const T (&g)[NP], const Loader &load, T mu,
+                                                   cpx<T> *cbuf, int r, int n, unsigned gmask) {
+    load_crow<NP, T>(a, load, r, n);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        a[k] = mk<T>(g[k] * a[k].x, g[k] * a[k].y);
+        if (k == r) a[k].x -= mu;
+    }
+    gj_invert<NP, T, cpx<T>, false>(a, cbuf, r, n, gmask);
+}
+
+// Solve one pixel.  T = float: returns flag = true (and no outputs) for a pixel
+// whose single-precision result cannot be trusted to err_max, when
+// prm.fp64_resolve is set.  T = double: always produces outputs; the inversion
+// of G fails (EVD fallback) when a pivot is <= 1e-12, the limit of the FP64
+// reference.
+//
+// Shift: inverse iteration starts with mu (0.99, Sec. III-B).  When the
+// iterate converges slowly (factor q > 0.3 after 4 steps, i.e. lambda_min sits
+// far above mu relative to the gap), the shift moves 3/4 of the way to the
+// current eigenvalue estimate mu + 1/(x^H B^{-1} x) (an upper bound of
+// lambda_min while B is positive definite) and B^{-1} is rebuilt; at most
+// three times.
+//
+// Error bound: a relative perturbation e of G moves G^{-1} by about
+// cond(G) |G^{-1}| e and the eigenvector by that over the eigengap; the gap is
+// read off the observed convergence factor q = (l1 - mu)/(l2 - mu).  The bound
+// is first order and loose (on synthetic stacks the measured single-precision
+// error sits three to four orders of magnitude below it), so pixels are handed
+// to double precision when it exceeds err_max (default 0.1).
 template <int NP, class T, class Loader>
 __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, const EmiParams &prm,
                                  cpx<T> *cbuf, unsigned gmask, int glane0, bool is_fp64) {
@@ -191,7 +226,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     cpx<T> a[NP];
     load_crow<NP, T>(a, load, r, n);
 
-    // G = (1 - beta)|C| + beta I, and its inverse.
+    // G = (1 - beta)|C| + beta I, and its inverse (kept in g).
     T g[NP];
     T rs = 0;
 #pragma unroll
@@ -210,21 +245,30 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     const T cond = norm_g * norm_gi;
     const bool finite = isfinite(cond);
 
-    if (!is_fp64 && prm.fp64_resolve &&
+    // Rank one (a single look, e.g. an isolated persistent scatterer): every
+    // |C_ik| is 1 to rounding, G is singular, and the EVD fallback's answer is
+    // exact in single precision.  Any other singular-looking G goes to the
+    // double-precision path, which applies the reference pivot limit.
+    bool rank_one = false;
+    if (!is_fp64 && (minpiv <= Lim<T>::piv_flag || !finite)) {
+        T mmin = T(1);
+        load_crow<NP, T>(a, load, r, n);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) mmin = fmin(mmin, sqrt_t(norm2(a[k])) + ((k == r || k >= n || !live) ? T(1) : T(0)));
+        rank_one = group_min<NP, T>(mmin, gmask) >= T(1) - T(8) * Eps<T>::v;
+    }
+    if (!is_fp64 && prm.fp64_resolve && !rank_one &&
         (minpiv <= Lim<T>::piv_flag || !finite || cond > T(prm.cond_max))) {
         out.flag = true;
         return out;
     }
-    const bool inv_failed = (minpiv <= Lim<T>::piv_fail) || !finite;
+    const bool inv_failed = rank_one || (minpiv <= Lim<T>::piv_fail) || !finite;
 
-    // Iteration matrix: B^{-1} = (G^{-1} o C - mu I)^{-1}; C itself on fallback.
-    if (!inv_failed) {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            a[k] = mk<T>(g[k] * a[k].x, g[k] * a[k].y);
-            if (k == r) a[k].x -= T(prm.mu);
-        }
-        gj_invert<NP, T, cpx<T>, false>(a, cbuf, r, n, gmask);
+    T mu = T(prm.mu);
+    if (inv_failed) {
+        load_crow<NP, T>(a, load, r, n);  // EVD fallback: power iteration on C
+    } else {
+        form_shift_inverse<NP, T>(a, g, load, mu, cbuf, r, n, gmask);
     }
 
     // Start vector: phases of column 0 of C (the interferograms to entry 0).
@@ -239,6 +283,8 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     const T tol2 = tol * tol;
     cpx<T> d = mk<T>(T(1), T(0));
     bool conv = false;
+    T dl_prev = T(-1), q = T(0);
+    int in_round = 0, reshifts = 0;
     for (int it = 0; it < prm.max_iter; ++it) {
         cpx<T> y = group_matvec<NP, T>(a, x, cbuf, r, gmask);
         if (!live) y = mk<T>(T(0), T(0));
@@ -251,13 +297,40 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         const cpx<T> yn = (sc > T(0)) ? sc * (y * conj(d)) : x;
         const T dl = group_sum<NP, T>(norm2(yn - x), gmask);
         x = yn;
+        ++in_round;
+        if (dl_prev > T(0) && dl > T(100) * tol2) q = sqrt_t(dl / dl_prev);
+        dl_prev = dl;
         if (dl <= tol2) {
             conv = true;
             break;
         }
+        if (!inv_failed && reshifts < 3 && in_round >= 4 && q > T(0.3)) {
+            const T lam_est = mu + T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
+            mu = mu + T(0.75) * (lam_est - mu);
+            form_shift_inverse<NP, T>(a, g, load, mu, cbuf, r, n, gmask);
+            ++reshifts;
+            in_round = 0;
+            dl_prev = T(-1);
+            q = T(0);
+        }
     }
     // x^H B^{-1} x = 1 / (lambda - mu) at convergence (EMI); x^H C x on fallback.
-    const T lam = T(prm.mu) + T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
+    const T theta = T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
+    const T lam = inv_failed ? d.x : mu + theta;
+
+    if (!is_fp64 && prm.fp64_resolve && !inv_failed) {
+        // gap = lambda_2 - lambda_1 from q = theta / (lambda_2 - mu)
+        const T gap = (q > T(0)) ? abs_t(theta) * (T(1) / q - T(1)) : abs_t(theta) * T(1e3);
+        const T est = T(4) * Eps<T>::v * cond * norm_gi / fmax(gap, Lim<T>::tiny);
+#ifdef PLK_DEBUG_EST
+        out.lam = (float)est;  // diagnostic builds export the estimate instead of flagging
+#else
+        if (!conv || !(est <= T(prm.err_max))) {
+            out.flag = true;
+            return out;
+        }
+#endif
+    }
 
     // Reference (Sec. II-A): phihat_i = arg(v_i conj(v_ref)), phihat_ref = 0.
     cpx<T> vr;
@@ -273,14 +346,13 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     cpx<T> zeta = (wm2 > T(0)) ? (rsqrt_t(wm2) * w) : mk<T>(T(1), T(0));
     if (r == ref) zeta = mk<T>(T(1), T(0));
     load_crow<NP, T>(a, load, r, n);
-    cpx<T> u[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const T m2 = norm2(a[k]);
         const cpx<T> uk = (m2 > T(0)) ? (rsqrt_t(m2) * a[k]) : mk<T>(T(1), T(0));
-        u[k] = (k > r && k < n) ? uk : mk<T>(T(0), T(0));
+        a[k] = (k > r && k < n) ? uk : mk<T>(T(0), T(0));
     }
-    const cpx<T> rowsum = group_matvec<NP, T>(u, zeta, cbuf, r, gmask);
+    const cpx<T> rowsum = group_matvec<NP, T>(a, zeta, cbuf, r, gmask);
     const cpx<T> term = live ? (conj(zeta) * rowsum) : mk<T>(T(0), T(0));
     const T sx = group_sum<NP, T>(term.x, gmask);
     const T sy = group_sum<NP, T>(term.y, gmask);
@@ -288,7 +360,11 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
 
     out.phase = (float)ph;
     out.tcoh = (float)tcoh;
+#ifndef PLK_DEBUG_EST
     out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
+#else
+    if (is_fp64 || inv_failed) out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
+#endif
     out.status = inv_failed ? PLK_PX_EVD : (!conv ? PLK_PX_NOCONV : (is_fp64 ? PLK_PX_EMI_FP64 : PLK_PX_EMI));
     return out;
 }

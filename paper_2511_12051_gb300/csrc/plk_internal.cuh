@@ -35,7 +35,7 @@ inline Geom make_geom(int H, int W, plk_window w) {
 
 // Parameters of the phase-linking kernels, resolved on the host.
 struct EmiParams {
-    float beta, mu, tol, cond_max;
+    float beta, mu, tol, cond_max, err_max;
     int max_iter;
     int fp64_resolve;
 };
@@ -54,11 +54,35 @@ cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *m
 // shared memory even at a 1x1 output tile.
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                               cudaStream_t s);
+struct Prof;
 cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
-                              float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s);
+                              float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s,
+                              Prof *prof = nullptr);
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
                             float2 *kappa, cudaStream_t s);
 
 int device_sm_count();
+
+// Optional per-launch timing: events recorded on the launching stream around
+// each kernel while enabled (see plk_profile_enable).
+struct Prof {
+    static constexpr int kMaxRecords = 4096;
+    bool on = false;
+    int n = 0;
+    cudaEvent_t ev[2 * kMaxRecords] = {};
+    const char *name[kMaxRecords] = {};
+    bool overflow = false;
+    void begin(const char *nm, cudaStream_t s) {
+        if (!on) return;
+        if (n >= kMaxRecords) { overflow = true; return; }
+        name[n] = nm;
+        cudaEventRecord(ev[2 * n], s);
+    }
+    void end(cudaStream_t s) {
+        if (!on || n >= kMaxRecords) return;
+        cudaEventRecord(ev[2 * n + 1], s);
+        ++n;
+    }
+};
 
 }  // namespace plk

@@ -18,7 +18,9 @@ import threading
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libplk.so")
+# PLK_LIB_PATH selects another build of the same library (e.g. a variant built
+# with extra compile-time flags); by default the in-tree build is loaded.
+LIB_PATH = os.environ.get("PLK_LIB_PATH") or os.path.join(_HERE, "_build", "libplk.so")
 
 PLK_MAX_N = 32
 PX_EMI, PX_EMI_FP64, PX_EVD, PX_NODATA, PX_NOCONV = 0, 1, 2, 3, 4
@@ -38,7 +40,7 @@ class Window(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_float), ("mu", ctypes.c_float),
                 ("tol", ctypes.c_float), ("max_iter", ctypes.c_int32), ("cond_max", ctypes.c_float),
-                ("fp64_resolve", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("fp64_resolve", ctypes.c_int32), ("err_max", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
 
 
 _lock = threading.Lock()
@@ -66,6 +68,10 @@ _SIGS = {
     "plk_state_save": [_P, _P, ctypes.c_char_p],
     "plk_state_load": [_P, ctypes.c_char_p, _I, ctypes.POINTER(_P)],
     "plk_ministack_step": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
+    "plk_state_reset": [_P],
+    "plk_profile_enable": [_P, _I],
+    "plk_profile_collect": [_P, ctypes.POINTER(_I)],
+    "plk_profile_get": [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
 }
 EXPORTS = sorted(list(_SIGS) + ["plk_last_error", "plk_mask_words"])
 
@@ -173,6 +179,21 @@ class Context:
         except Exception:
             pass
 
+    # --------------------------------------------------------- kernel timing
+    def profile(self, enable: bool = True):
+        _check(lib().plk_profile_enable(self.h, int(enable)), self.h)
+
+    def profile_collect(self) -> dict:
+        """{stage: (total_ms, launches)} for the launches since the last collect."""
+        n = ctypes.c_int()
+        _check(lib().plk_profile_collect(self.h, ctypes.byref(n)), self.h)
+        out = {}
+        for i in range(n.value):
+            nm, ms, cnt = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int()
+            _check(lib().plk_profile_get(self.h, i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(cnt)))
+            out[nm.value.decode()] = (ms.value, cnt.value)
+        return out
+
     # ---------------------------------------------------------------- calls
     def amp_stats(self, slc: torch.Tensor, sum_pow: torch.Tensor | None = None,
                   sum_amp: torch.Tensor | None = None, accumulate: bool = False):
@@ -276,6 +297,9 @@ class State:
     def save(self, path: str):
         _check(lib().plk_state_save(self.ctx.h, self.h, os.fsencode(path)), self.ctx.h)
 
+    def reset(self):
+        _check(lib().plk_state_reset(self.h))
+
     def info(self) -> dict:
         k, n, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().plk_state_info(self.h, ctypes.byref(k), ctypes.byref(n), ctypes.byref(s)))
@@ -331,7 +355,7 @@ class _DevArray:
     """Minimal __cuda_array_interface__ view of a library-owned device buffer."""
 
     def __init__(self, ptr: int, shape, typestr: str):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 

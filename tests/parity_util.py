@@ -30,3 +30,19 @@ def phase_report(gpu_phase, orc_phase, valid=None):
     if d.size == 0:
         return {"max": 0.0, "p99": 0.0, "n": 0}
     return {"max": float(d.max()), "p99": float(np.percentile(d, 99)), "n": int(d.size)}
+
+
+def write_state_file(path, chain, M_max=None):
+    """Write an oracle chain's state in the library's checkpoint format
+    (magic, int32 header, ring oldest..newest as complex64, power and
+    amplitude sums as float32)."""
+    H, W = chain.H, chain.W
+    wy, wx, sy, sx = chain.window
+    hdr = np.array([H, W, wy, wx, sy, sx, chain.K_max, len(chain.ring), chain.n, 0], np.int32)
+    with open(path, "wb") as f:
+        f.write(b"PLKSTAT1")
+        f.write(hdr.tobytes())
+        for k in chain.ring:
+            f.write(np.ascontiguousarray(k, np.complex64).tobytes())
+        f.write(np.ascontiguousarray(chain.sum_pow, np.float32).tobytes())
+        f.write(np.ascontiguousarray(chain.sum_amp, np.float32).tobytes())

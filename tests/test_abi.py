@@ -57,7 +57,7 @@ def test_glrt_threshold_library_matches_oracle(libplk):
 def test_host_helpers(libplk):
     from paper_2511_12051_gb300 import plk
     p = plk.default_params()
-    assert p.alpha == pytest.approx(1e-3) and p.mu == pytest.approx(0.99) and p.max_iter == 50
+    assert p.alpha == pytest.approx(1e-3) and p.mu == pytest.approx(0.99) and p.max_iter == 100 and p.err_max == pytest.approx(0.1)
     assert plk.mask_words((5, 11, 3, 6)) == 1
     assert plk.mask_words((19, 37, 3, 6)) == 11
     Ho, Wo = ctypes.c_int(), ctypes.c_int()

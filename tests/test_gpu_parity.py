@@ -11,7 +11,8 @@ import torch
 
 import oracle
 from paper_2511_12051_gb300 import synth
-from parity_util import PHASE_TOL, TCOH_TOL, count_np, mask_np, phase_report, to_np, wrapped_diff
+from parity_util import (PHASE_TOL, TCOH_TOL, count_np, mask_np, phase_report, to_np, wrapped_diff,
+                         write_state_file)
 
 pytestmark = pytest.mark.gpu
 
@@ -144,47 +145,72 @@ def test_compress_parity(ctx, win, first_real):
 
 # ------------------------------------------------------------- S1-S8 chain
 
-def run_chain(plk, ctx, z, window, M, K_max, n_dates):
-    H, W = z.shape[1:]
-    st = plk.State(ctx, H, W, window, K_max=K_max, M_max=M)
-    orc = oracle.OracleChain(H, W, window, K_max=K_max, alpha=1e-3)
-    zg = z.cuda()
-    res = []
-    for sl in synth.ministack_slices(n_dates, M):
-        g = st.step(zg[sl].contiguous())
-        o = orc.step(z[sl].numpy())
-        res.append((g, o))
-    return res, st, orc
+def chain_case(case):
+    if case == "cfg0":
+        z, spec = stack(0, H=72, W=90)
+        return z, (5, 11, 1, 1), 10, 6, 10
+    if case == "cfg1":
+        z, spec = stack(1, H=96, W=300)
+        return z, (5, 11, 3, 6), 15, 6, 15
+    z, spec = stack(3, scale=0.05)  # 60 dates, 102 x 205, step patch inside
+    return z, (5, 11, 1, 1), 15, 3, 60
 
 
 @pytest.mark.parametrize("case", ["cfg0", "cfg1", "cfg3"])
-def test_ministack_chain_parity(plk, ctx, case):
-    if case == "cfg0":
-        z, spec = stack(0, H=72, W=90)
-        window, M, K_max, nd = (5, 11, 1, 1), 10, 6, 10
-    elif case == "cfg1":
-        z, spec = stack(1, H=96, W=300)
-        window, M, K_max, nd = (5, 11, 3, 6), 15, 6, 15
-    else:
-        z, spec = stack(3, scale=0.05)  # 60 dates, 102 x 204, step patch inside
-        window, M, K_max, nd = (5, 11, 1, 1), 15, 3, 60
-    res, st, orc = run_chain(plk, ctx, z, window, M, K_max, nd)
-    for k, (g, o) in enumerate(res):
+def test_ministack_step_parity(plk, ctx, case, tmp_path):
+    """Each step from identical inputs: the oracle's state (compressed SLCs as
+    stored complex64 samples, power sums) is loaded into the library through its
+    checkpoint format, and one step of both is compared."""
+    z, window, M, K_max, nd = chain_case(case)
+    H, W = z.shape[1:]
+    orc = oracle.OracleChain(H, W, window, K_max=K_max, alpha=1e-3, kappa_dtype=np.complex64)
+    zg = z.cuda()
+    for k, sl in enumerate(synth.ministack_slices(nd, M)):
+        path = str(tmp_path / f"s{k}.plk")
+        write_state_file(path, orc)
+        st = plk.State.load(ctx, path, M_max=M)
+        g = st.step(zg[sl].contiguous())
+        o = orc.step(z[sl].numpy())
         assert np.array_equal(count_np(g["count"]), o["count"]), k
         live = o["status"] != 3
+        assert np.array_equal(to_np(g["status"]) == 3, ~live)
         clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
         K = o["K_used"]
         rep = phase_report(to_np(g["phase"]), o["phase"][K:], clear)
         assert rep["max"] <= PHASE_TOL, (k, rep)
         tc = np.abs(to_np(g["tcoh"]) - o["tcoh"])[live]
         assert tc.max() <= TCOH_TOL, (k, tc.max())
+        assert clear.sum() >= 0.99 * live.sum()
+        # the new compressed SLC
+        kg = to_np(st.kappa(st.info()["K_used"] - 1))
+        ko = orc.ring[-1]
+        scale = np.abs(z[sl].numpy()).sum(0)
+        assert np.max(np.abs(kg - ko) / (scale + 1e-6)) < 1e-4
+        assert np.array_equal(to_np(st.sum_pow()), orc.sum_pow)
+        st.close()
+
+
+@pytest.mark.parametrize("case", ["cfg1", "cfg3"])
+def test_ministack_chain_end_to_end(plk, ctx, case):
+    """The whole chain, each side carrying its own compressed SLCs: single-
+    precision differences in kappa propagate, so the bar is statistical
+    (p99 within the phase tolerance) plus exact masks and power sums."""
+    z, window, M, K_max, nd = chain_case(case)
+    H, W = z.shape[1:]
+    st = plk.State(ctx, H, W, window, K_max=K_max, M_max=M)
+    orc = oracle.OracleChain(H, W, window, K_max=K_max, alpha=1e-3)
+    zg = z.cuda()
+    for k, sl in enumerate(synth.ministack_slices(nd, M)):
+        g = st.step(zg[sl].contiguous())
+        o = orc.step(z[sl].numpy())
+        assert np.array_equal(count_np(g["count"]), o["count"]), k
+        live = o["status"] != 3
+        K = o["K_used"]
+        d = wrapped_diff(to_np(g["phase"]), o["phase"][K:])[:, live]
+        assert np.percentile(d, 99) <= PHASE_TOL, (k, np.percentile(d, 99))
+        assert np.median(d) <= 0.1 * PHASE_TOL
     info = st.info()
-    assert info["n_eff"] == nd and info["K_used"] == min(K_max, len(res))
-    # the ring holds the same compressed SLCs (single vs double precision)
-    for i in range(info["K_used"]):
-        kg = to_np(st.kappa(i))
-        ko = orc.ring[i]
-        assert np.max(np.abs(kg - ko)) <= 1e-4 * np.max(np.abs(ko))
+    assert info["n_eff"] == nd and info["K_used"] == min(K_max, len(synth.ministack_slices(nd, M)))
     assert np.array_equal(to_np(st.sum_pow()), orc.sum_pow)
 
 
@@ -206,7 +232,7 @@ def test_chain_checkpoint_resume(plk, ctx, tmp_path):
     for ga, gc in zip(outs_a[2:], outs_c):
         assert torch.equal(ga["phase"], gc["phase"])
         assert torch.equal(ga["tcoh"], gc["tcoh"])
-    assert c.info() == a.info() | {"steps": 4}
+    assert c.info() == a.info()
 
 
 # ------------------------------------------------------------------ edges
