@@ -602,7 +602,8 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
         return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: window with N=%d exceeds shared memory", N);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: covariance");
     const int ref = K > 0 ? K - 1 : 0;
-    e = plk::launch_phase_link(st->C, N, nout, ref, prm, st->phase_all, tcoh, nullptr, status, s, &ctx->prof);
+    const plk::StackSource src{&z, &g, st->mask};
+    e = plk::launch_phase_link(st->C, N, nout, ref, prm, st->phase_all, tcoh, nullptr, status, s, &ctx->prof, &src);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: phase_link");
     if (nout > 0) {
         e = cudaMemcpyAsync(phase, st->phase_all + (long long)K * nout, (size_t)M * nout * sizeof(float),

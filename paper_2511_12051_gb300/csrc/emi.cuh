@@ -88,50 +88,62 @@ __device__ __forceinline__ double real_s(double, double v) { return v; }
 template <class T>
 __device__ __forceinline__ cpx<T> real_s(cpx<T>, T v) { return mk<T>(v, T(0)); }
 
-// In-place Gauss-Jordan inverse of the n x n leading block of a matrix whose
-// row r is a[] (lane r of the group).  Step k: lane k publishes row k divided
-// by the pivot, with entry k replaced by 1/pivot; every lane then eliminates
-// its column-k entry while streaming the published row in 16-byte chunks.
-// PD = true (the real G): pivots are expected positive; a pivot <= `tiny` is
-// replaced by `tiny`.  PD = false (complex B, possibly indefinite): only a
-// pivot of magnitude below `tiny` is replaced.  Returns, in every lane, the
-// smallest real pivot met (before replacement).
+// In-place Gauss-Jordan inverse (no pivoting) of the matrix whose row r is
+// held by lane r of the group.  The step loop is not unrolled, so the pivot
+// column cannot be a runtime register index; instead each lane keeps its row
+// rotated: at step k, a[c] holds column (k + c) mod NP, so the pivot column is
+// always a[0].  Step k: lane k publishes its row divided by the pivot (entry 0
+// replaced by 1/pivot); every lane eliminates with it and shifts its row one
+// place left, the freed slot taking the new inverse column.  After NP steps
+// the rotation is complete and a[c] holds column c of the inverse.  Padded
+// rows/columns (index >= n) are the identity: their steps have pivot 1 and
+// leave the n x n block untouched.
+// PD = true (real G): pivots are expected positive; a pivot <= tiny is
+// replaced by tiny.  PD = false (complex B, possibly indefinite): only a pivot
+// of magnitude below tiny is replaced.  Returns, in every lane, the smallest
+// real pivot met over the first n steps (before replacement).
 template <int NP, class T, class S, bool PD>
 __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigned gmask) {
     constexpr int E = 16 / sizeof(S);
     static_assert(NP % E == 0, "row must be a multiple of 16 bytes");
     T minpiv = Lim<T>::big;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < NP; ++k) {
-        if (k >= n) break;
         if (r == k) {
-            S piv = a[k];
+            S piv = a[0];
             const T pr = re_s(piv);
-            minpiv = fmin(minpiv, pr);
+            if (k < n) minpiv = fmin(minpiv, pr);
             if (PD) {
                 if (!(pr > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
             } else {
                 if (!(abs_t(pr) > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
             }
             const S inv = inv_s(piv);
+            buf[0] = inv;
 #pragma unroll
-            for (int j = 0; j < NP; ++j) buf[j] = (j == k) ? inv : mul_s(a[j], inv);
+            for (int c = 1; c < NP; ++c) buf[c] = mul_s(a[c], inv);
         }
         __syncwarp(gmask);
-        const S f = a[k];
+        const S f = a[0];
+        const bool pivot_lane = (r == k);
         const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+        S last;
 #pragma unroll
         for (int q = 0; q < NP / E; ++q) {
             const uint4 v = src[q];
-            S rk[E];
-            memcpy(rk, &v, 16);
+            S p[E];
+            memcpy(p, &v, 16);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = q * E + e;
-                const S upd = (j == k) ? neg_s(mul_s(f, rk[e])) : fms_s(f, rk[e], a[j]);
-                a[j] = (r == k) ? rk[e] : upd;
+                if (j == 0) {
+                    last = pivot_lane ? p[0] : neg_s(mul_s(f, p[0]));
+                } else {
+                    a[j - 1] = pivot_lane ? p[e] : fms_s(f, p[e], a[j]);
+                }
             }
         }
+        a[NP - 1] = last;
         __syncwarp(gmask);
     }
     return group_min<NP, T>(minpiv, gmask);
@@ -184,16 +196,30 @@ __device__ __forceinline__ void load_crow(cpx<T> (&c)[NP], const Loader &load, i
 }
 
 // a <- (G^{-1} o C - mu I)^{-1}, from g = G^{-1} (this lane's row) and C.
+// Returns the smallest pivot: by Sylvester's law of inertia the pivots of the
+// Hermitian B = A - mu I (the D of its LDL^H factorisation) are all positive
+// exactly when B is positive definite, i.e. when mu lies below lambda_min.
 template <int NP, class T, class Loader>
-__device__ __forceinline__ void form_shift_inverse(cpx<T> (&a)[NP], const T (&g)[NP], const Loader &load, T mu,
-                                                   cpx<T> *cbuf, int r, int n, unsigned gmask) {
+__device__ __forceinline__ T form_shift_inverse(cpx<T> (&a)[NP], const T (&g)[NP], const Loader &load, T mu,
+                                                cpx<T> *cbuf, int r, int n, unsigned gmask) {
     load_crow<NP, T>(a, load, r, n);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         a[k] = mk<T>(g[k] * a[k].x, g[k] * a[k].y);
         if (k == r) a[k].x -= mu;
     }
-    gj_invert<NP, T, cpx<T>, false>(a, cbuf, r, n, gmask);
+    return gj_invert<NP, T, cpx<T>, false>(a, cbuf, r, n, gmask);
+}
+
+// y = A x with A = G^{-1} o C, row r from g and the reloaded C row.
+template <int NP, class T, class Loader>
+__device__ __forceinline__ cpx<T> apply_A(const T (&g)[NP], const Loader &load, cpx<T> x, cpx<T> *buf, int r,
+                                          int n, unsigned gmask) {
+    cpx<T> row[NP];
+    load_crow<NP, T>(row, load, r, n);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) row[k] = mk<T>(g[k] * row[k].x, g[k] * row[k].y);
+    return group_matvec<NP, T>(row, x, buf, r, gmask);
 }
 
 // Solve one pixel.  T = float: returns flag = true (and no outputs) for a pixel
@@ -279,7 +305,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         x = (m2 > T(0)) ? (rsqrt_t(m2) * c0) : mk<T>(T(1), T(0));
         x = live ? (rsqrt_t(T(n)) * x) : mk<T>(T(0), T(0));
     }
-    const T tol = is_fp64 ? T(1e-10) : T(prm.tol);
+    const T tol = is_fp64 ? T(1e-9) : T(prm.tol);
     const T tol2 = tol * tol;
     cpx<T> d = mk<T>(T(1), T(0));
     bool conv = false;
@@ -305,14 +331,35 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
             break;
         }
         if (!inv_failed && reshifts < 3 && in_round >= 4 && q > T(0.3)) {
+            // Move the shift towards lambda_min; keep the new shift only if
+            // B stays positive definite (the shift is still below lambda_min),
+            // otherwise restore the previous one and stop moving it.
             const T lam_est = mu + T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
-            mu = mu + T(0.75) * (lam_est - mu);
-            form_shift_inverse<NP, T>(a, g, load, mu, cbuf, r, n, gmask);
-            ++reshifts;
+            const T mu_new = mu + T(0.75) * (lam_est - mu);
+            const T pmin = form_shift_inverse<NP, T>(a, g, load, mu_new, cbuf, r, n, gmask);
+            if (pmin > T(0)) {
+                mu = mu_new;
+                ++reshifts;
+            } else {
+                form_shift_inverse<NP, T>(a, g, load, mu, cbuf, r, n, gmask);
+                reshifts = 3;
+            }
             in_round = 0;
             dl_prev = T(-1);
             q = T(0);
         }
+    }
+    if (!inv_failed && conv) {
+        // Residual correction against A itself: x <- x - B^{-1} (A x - rho x).
+        // Its fixed point is an exact eigenvector of A, whatever the rounding
+        // of the computed B^{-1} (preconditioned inverse iteration).
+        const cpx<T> ax = apply_A<NP, T>(g, load, x, cbuf, r, n, gmask);
+        const T rho = group_sum<NP, T>(live ? (x.x * ax.x + x.y * ax.y) : T(0), gmask);
+        const cpx<T> res = live ? (ax - rho * x) : mk<T>(T(0), T(0));
+        cpx<T> corr = group_matvec<NP, T>(a, res, cbuf, r, gmask);
+        cpx<T> xn = live ? (x - corr) : mk<T>(T(0), T(0));
+        const T s2 = group_sum<NP, T>(norm2(xn), gmask);
+        if (s2 > T(0)) x = rsqrt_t(s2) * xn;
     }
     // x^H B^{-1} x = 1 / (lambda - mu) at convergence (EMI); x^H C x on fallback.
     const T theta = T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);

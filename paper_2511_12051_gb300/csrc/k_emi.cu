@@ -19,11 +19,15 @@ struct PackedRow {
 };
 
 constexpr int kEmiWarps = 4;
+// CTAs per SM the single-precision kernel is register-budgeted for (NP <= 16).
+#ifndef PLK_EMI_MINB
+#define PLK_EMI_MINB 4
+#endif
 
 // Single-precision pass: one NP-lane group per pixel.  Pixels the solve flags
 // get status kPending and no other output.
 template <int NP>
-__global__ void __launch_bounds__(kEmiWarps * 32) k_emi32(const float2 *__restrict__ C, int n, long long npx,
+__global__ void __launch_bounds__(kEmiWarps * 32, NP == 32 ? 1 : PLK_EMI_MINB) k_emi32(const float2 *__restrict__ C, int n, long long npx,
                                                           int ref, const EmiParams prm,
                                                           float *__restrict__ phase, float *__restrict__ tcoh,
                                                           float *__restrict__ lam, uint8_t *__restrict__ status) {
@@ -116,9 +120,121 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restri
     }
 }
 
+// Row source held in registers (indexed with compile-time k after inlining).
+template <int NP, class T>
+struct RegRow {
+    cpx<T> c[NP];
+    __device__ __forceinline__ cpx<T> operator()(int k) const { return c[k]; }
+};
+
+// Double-precision re-solve for the mini-stack path: the coherence row of a
+// pending pixel is recomputed from the SLC stack over its SHP neighbourhood,
+// in double precision (products of single-precision samples are exact in
+// double), so the solve sees the same coherence as an FP64 reference instead
+// of the single-precision one.
+template <int NP>
+__global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_constant__ Planes z, const Geom g,
+                                                                const uint64_t *__restrict__ mask, int n,
+                                                                long long npx, int ref, const EmiParams prm,
+                                                                float *__restrict__ phase, float *__restrict__ tcoh,
+                                                                float *__restrict__ lam,
+                                                                uint8_t *__restrict__ status) {
+    constexpr int G = 32 / NP;
+    constexpr int E = 16 / sizeof(cpx<double>);
+    __shared__ __align__(16) cpx<double> sbuf[kEmiWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / NP, r = lane - grp * NP;
+    const int glane0 = grp * NP;
+    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const long long step = (long long)gridDim.x * kEmiWarps * 32;
+
+    for (long long base = ((long long)blockIdx.x * kEmiWarps + warp) * 32; base < npx; base += step) {
+        const long long pl = base + lane;
+        const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
+        unsigned bal = __ballot_sync(0xffffffffu, pend);
+        while (bal) {
+            int mine = -1;
+#pragma unroll
+            for (int gg = 0; gg < G; ++gg) {
+                if (bal) {
+                    const int b = __ffs(bal) - 1;
+                    if (gg == grp) mine = b;
+                    bal &= bal - 1u;
+                }
+            }
+            if (mine >= 0) {
+                const long long p = base + mine;
+                const int oy = (int)(p / g.Wo), ox = (int)(p - (p / g.Wo) * g.Wo);
+                const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
+                const uint64_t *mw = mask + p * g.nwords;
+                RegRow<NP, double> row;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) row.c[k] = mk<double>(0.0, 0.0);
+                int b = 0;
+                uint64_t word = __ldg(mw);
+                for (int dy = -g.hy; dy <= g.hy; ++dy)
+                    for (int dx = -g.hx; dx <= g.hx; ++dx, ++b) {
+                        if ((b & 63) == 0 && b > 0) word = __ldg(mw + (b >> 6));
+                        if (!((word >> (b & 63)) & 1ull)) continue;
+                        const long long q = (long long)(cy + dy) * g.W + (cx + dx);
+                        float2 zr = make_float2(0.f, 0.f);
+                        if (r < n) zr = __ldg(z.p[r] + q);
+                        const double xr = zr.x, yr = zr.y;
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) {
+                            if (k < n) {
+                                const float2 zk = __ldg(z.p[k] + q);
+                                const double xk = zk.x, yk = zk.y;
+                                row.c[k].x += xr * xk + yr * yk;
+                                row.c[k].y += yr * xk - xr * yk;
+                            }
+                        }
+                    }
+                // normalise: C_rk = S_rk / sqrt(S_rr S_kk), C_rr = 1
+                cpx<double> *buf = &sbuf[warp][glane0];
+                double d_own = 0.0;
+#pragma unroll
+                for (int k = 0; k < NP; ++k)
+                    if (k == r) d_own = row.c[k].x;
+                buf[r] = mk<double>(d_own, 0.0);
+                __syncwarp(gmask);
+                const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+#pragma unroll
+                for (int q4 = 0; q4 < NP / E; ++q4) {
+                    const uint4 v = src[q4];
+                    cpx<double> dk[E];
+                    memcpy(dk, &v, 16);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int k = q4 * E + e;
+                        const double prod = d_own * dk[e].x;
+                        cpx<double> cv;
+                        if (k == r) cv = mk<double>(1.0, 0.0);
+                        else if (d_own > 0.0 && dk[e].x > 0.0) {
+                            const double s = 1.0 / sqrt(prod);
+                            cv = mk<double>(row.c[k].x * s, row.c[k].y * s);
+                        } else cv = mk<double>(0.0, 0.0);
+                        row.c[k] = cv;
+                    }
+                }
+                __syncwarp(gmask);
+                const PixelResult res = emi_solve<NP, double>(row, r, n, ref, prm, buf, gmask, glane0, true);
+                if (r < n) phase[(long long)r * npx + p] = res.phase;
+                if (r == 0) {
+                    if (tcoh) tcoh[p] = res.tcoh;
+                    if (lam) lam[p] = res.lam;
+                    status[p] = (uint8_t)res.status;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 template <int NP>
 static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const EmiParams &prm, float *phase,
-                           float *tcoh, float *lam, uint8_t *status, cudaStream_t s, Prof *prof) {
+                           float *tcoh, float *lam, uint8_t *status, cudaStream_t s, Prof *prof,
+                           const StackSource *src) {
     constexpr int G = 32 / NP;
     const long long cap = (long long)device_sm_count() * 16;
     long long blocks = ((npx + G - 1) / G + kEmiWarps - 1) / kEmiWarps;
@@ -131,18 +247,23 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
     long long blocks64 = ((npx + 31) / 32 + kEmiWarps - 1) / kEmiWarps;
     blocks64 = blocks64 > cap ? cap : (blocks64 < 1 ? 1 : blocks64);
     if (prof) prof->begin("phase_link_fp64", s);
-    k_emi64<NP><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status);
+    if (src)
+        k_emi64_stack<NP><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(*src->z, *src->g, src->mask, n, npx, ref, prm,
+                                                                        phase, tcoh, lam, status);
+    else
+        k_emi64<NP><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status);
     e = cudaGetLastError();
     if (prof) prof->end(s);
     return e;
 }
 
 cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
-                              float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s, Prof *prof) {
+                              float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s, Prof *prof,
+                              const StackSource *src) {
     if (npx == 0) return cudaSuccess;
-    if (n <= 8) return run_emi<8>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof);
-    if (n <= 16) return run_emi<16>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof);
-    return run_emi<32>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof);
+    if (n <= 8) return run_emi<8>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+    if (n <= 16) return run_emi<16>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+    return run_emi<32>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
 }
 
 }  // namespace plk

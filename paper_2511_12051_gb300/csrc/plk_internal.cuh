@@ -55,9 +55,16 @@ cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *m
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                               cudaStream_t s);
 struct Prof;
+// Where the double-precision re-solve recomputes a pixel's coherence from:
+// the stack planes, geometry and SHP masks of the mini-stack.
+struct StackSource {
+    const Planes *z;
+    const Geom *g;
+    const uint64_t *mask;
+};
 cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
                               float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s,
-                              Prof *prof = nullptr);
+                              Prof *prof = nullptr, const StackSource *src = nullptr);
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
                             float2 *kappa, cudaStream_t s);
 
