@@ -219,6 +219,37 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
                               const plk_params *params, float *phase, float *tcoh,
                               uint8_t *status, uint16_t *shp_count);
 
+/* ------------------------------------------- allocation-free variant */
+
+/* Scratch capacity of plk_phase_link_stack_noalloc, in bytes: one array of
+ * this size is held on every device that loads the library, until exit. */
+#define PLK_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* One mini-stack of N real SLCs slc [N][H][W] through S1-S6 (amplitude sums,
+ * GLRT SHP with n_eff = N, coherence, EMI with reference ref_idx, gamma_t)
+ * without allocating any device memory.  No counterpart in the paper: this is
+ * for callers that cannot call cudaMalloc, for example a plug-in running
+ * inside a host application that owns every device allocation, or a service
+ * that must not allocate after start-up.  Outputs as plk_phase_link:
+ * phase [N][Ho][Wo], tcoh and status [Ho][Wo]; shp_count [Ho][Wo] may be NULL.
+ * Results equal those of plk_ministack_step on a fresh state (ref_idx = 0).
+ * Work is issued on cuda_stream on the CURRENT device.
+ * Scratch: sums, masks, counts and coherence live in a file-scope device array
+ * of PLK_NOALLOC_SCRATCH_BYTES shared by every call; inputs and outputs stay
+ * the caller's.  A request needing more (about 1 KB per output pixel at N=15
+ * plus 4 bytes per input pixel) returns PLK_EINVAL with the sizes in
+ * plk_last_error(NULL).  Every scratch region is written in full before it is
+ * read within a call, so nothing needs clearing; calls that overlap on the
+ * GPU (other streams, other threads) race on the shared array and must be
+ * serialized by the caller.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and keeps it; make that first call
+ * before any stream capture.  Errors: EINVAL (bad argument, too large),
+ * EUNSUPPORTED, ECUDA; text in plk_last_error(NULL). */
+plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, int H, int W, plk_window win,
+                                        int ref_idx, const plk_params *params, float *phase,
+                                        float *tcoh, uint8_t *status, uint16_t *shp_count,
+                                        void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,11 @@ double inc_beta_cf(double a, double b, double x) {
 
 namespace plk {
 
+void set_noctx_error(const char *msg) {
+    strncpy(g_noctx_err, msg, sizeof(g_noctx_err) - 1);
+    g_noctx_err[sizeof(g_noctx_err) - 1] = 0;
+}
+
 int device_sm_count() {
     static int cache[64] = {0};
     int dev = 0;

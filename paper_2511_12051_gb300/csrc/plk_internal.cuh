@@ -69,6 +69,8 @@ cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &
                             float2 *kappa, cudaStream_t s);
 
 int device_sm_count();
+// Text returned by plk_last_error(NULL) on this thread.
+void set_noctx_error(const char *msg);
 
 // Optional per-launch timing: events recorded on the launching stream around
 // each kernel while enabled (see plk_profile_enable).

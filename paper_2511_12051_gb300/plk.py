@@ -72,6 +72,7 @@ _SIGS = {
     "plk_profile_enable": [_P, _I],
     "plk_profile_collect": [_P, ctypes.POINTER(_I)],
     "plk_profile_get": [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
+    "plk_phase_link_stack_noalloc": [_P, _I, _I, _I, Window, _I, ctypes.POINTER(Params), _P, _P, _P, _P, _P],
 }
 EXPORTS = sorted(list(_SIGS) + ["plk_last_error", "plk_mask_words"])
 
