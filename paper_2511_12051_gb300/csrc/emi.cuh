@@ -222,6 +222,58 @@ __device__ __forceinline__ cpx<T> apply_A(const T (&g)[NP], const Loader &load, 
     return group_matvec<NP, T>(row, x, buf, r, gmask);
 }
 
+// Inverse iteration x <- B^{-1} x / |B^{-1} x| on the rows a[] (B^{-1}, or C
+// itself on the EVD fallback when allow_reshift is false), with the shift
+// refinement described at emi_solve: reform(mu) rebuilds a[] for a new shift
+// and returns the smallest pivot.  On return d = x^H a x of the last step
+// (1/(lambda - mu) for B^{-1}) and q the last convergence factor measured
+// above the noise floor.  Returns true on convergence.
+template <int NP, class T, class Reform>
+__device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cpx<T> &d, T &mu, T &q,
+                                                  const Reform &reform, bool allow_reshift, cpx<T> *cbuf, int r,
+                                                  bool live, unsigned gmask, T tol, int max_iter) {
+    const T tol2 = tol * tol;
+    d = mk<T>(T(1), T(0));
+    q = T(0);
+    T dl_prev = T(-1);
+    int in_round = 0, reshifts = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        cpx<T> y = group_matvec<NP, T>(a, x, cbuf, r, gmask);
+        if (!live) y = mk<T>(T(0), T(0));
+        const T s = group_sum<NP, T>(norm2(y), gmask);          // |y|^2
+        d.x = group_sum<NP, T>(x.x * y.x + x.y * y.y, gmask);  // x^H y
+        d.y = group_sum<NP, T>(x.x * y.y - x.y * y.x, gmask);
+        const T dm2 = norm2(d);
+        // Unit iterate with x's common phase: y conj(d) / (|d| |y|).
+        const T sc = (s > T(0) && dm2 > T(0)) ? rsqrt_t(s) * rsqrt_t(dm2) : T(0);
+        const cpx<T> yn = (sc > T(0)) ? sc * (y * conj(d)) : x;
+        const T dl = group_sum<NP, T>(norm2(yn - x), gmask);
+        x = yn;
+        ++in_round;
+        if (dl_prev > T(0) && dl > T(100) * tol2) q = sqrt_t(dl / dl_prev);
+        dl_prev = dl;
+        if (dl <= tol2) return true;
+        if (allow_reshift && reshifts < 3 && in_round >= 4 && q > T(0.3)) {
+            // Move the shift towards lambda_min; keep it only if B stays
+            // positive definite (the shift is still below lambda_min),
+            // otherwise restore the previous one and stop moving it.
+            const T lam_est = mu + T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
+            const T mu_new = mu + T(0.75) * (lam_est - mu);
+            if (reform(mu_new) > T(0)) {
+                mu = mu_new;
+                ++reshifts;
+            } else {
+                reform(mu);
+                reshifts = 3;
+            }
+            in_round = 0;
+            dl_prev = T(-1);
+            q = T(0);
+        }
+    }
+    return false;
+}
+
 // Solve one pixel.  T = float: returns flag = true (and no outputs) for a pixel
 // whose single-precision result cannot be trusted to err_max, when
 // prm.fp64_resolve is set.  T = double: always produces outputs; the inversion
@@ -281,7 +333,9 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         load_crow<NP, T>(a, load, r, n);
 #pragma unroll
         for (int k = 0; k < NP; ++k) mmin = fmin(mmin, sqrt_t(norm2(a[k])) + ((k == r || k >= n || !live) ? T(1) : T(0)));
-        rank_one = group_min<NP, T>(mmin, gmask) >= T(1) - T(8) * Eps<T>::v;
+        // |C_ik| of a single look is 1 up to the rounding of the products and
+        // reciprocal square roots that normalise it (a few ulps each).
+        rank_one = group_min<NP, T>(mmin, gmask) >= T(1) - T(64) * Eps<T>::v;
     }
     if (!is_fp64 && prm.fp64_resolve && !rank_one &&
         (minpiv <= Lim<T>::piv_flag || !finite || cond > T(prm.cond_max))) {
@@ -306,49 +360,11 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         x = live ? (rsqrt_t(T(n)) * x) : mk<T>(T(0), T(0));
     }
     const T tol = is_fp64 ? T(1e-9) : T(prm.tol);
-    const T tol2 = tol * tol;
-    cpx<T> d = mk<T>(T(1), T(0));
-    bool conv = false;
-    T dl_prev = T(-1), q = T(0);
-    int in_round = 0, reshifts = 0;
-    for (int it = 0; it < prm.max_iter; ++it) {
-        cpx<T> y = group_matvec<NP, T>(a, x, cbuf, r, gmask);
-        if (!live) y = mk<T>(T(0), T(0));
-        const T s = group_sum<NP, T>(norm2(y), gmask);          // |y|^2
-        d.x = group_sum<NP, T>(x.x * y.x + x.y * y.y, gmask);  // x^H y
-        d.y = group_sum<NP, T>(x.x * y.y - x.y * y.x, gmask);
-        const T dm2 = norm2(d);
-        // Unit iterate with x's common phase: y conj(d) / (|d| |y|).
-        const T sc = (s > T(0) && dm2 > T(0)) ? rsqrt_t(s) * rsqrt_t(dm2) : T(0);
-        const cpx<T> yn = (sc > T(0)) ? sc * (y * conj(d)) : x;
-        const T dl = group_sum<NP, T>(norm2(yn - x), gmask);
-        x = yn;
-        ++in_round;
-        if (dl_prev > T(0) && dl > T(100) * tol2) q = sqrt_t(dl / dl_prev);
-        dl_prev = dl;
-        if (dl <= tol2) {
-            conv = true;
-            break;
-        }
-        if (!inv_failed && reshifts < 3 && in_round >= 4 && q > T(0.3)) {
-            // Move the shift towards lambda_min; keep the new shift only if
-            // B stays positive definite (the shift is still below lambda_min),
-            // otherwise restore the previous one and stop moving it.
-            const T lam_est = mu + T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
-            const T mu_new = mu + T(0.75) * (lam_est - mu);
-            const T pmin = form_shift_inverse<NP, T>(a, g, load, mu_new, cbuf, r, n, gmask);
-            if (pmin > T(0)) {
-                mu = mu_new;
-                ++reshifts;
-            } else {
-                form_shift_inverse<NP, T>(a, g, load, mu, cbuf, r, n, gmask);
-                reshifts = 3;
-            }
-            in_round = 0;
-            dl_prev = T(-1);
-            q = T(0);
-        }
-    }
+    cpx<T> d;
+    T q;
+    auto reform = [&](T m) { return form_shift_inverse<NP, T>(a, g, load, m, cbuf, r, n, gmask); };
+    const bool conv = inverse_iteration<NP, T>(a, x, d, mu, q, reform, !inv_failed, cbuf, r, live, gmask, tol,
+                                               prm.max_iter);
     if (!inv_failed && conv) {
         // Residual correction against A itself: x <- x - B^{-1} (A x - rho x).
         // Its fixed point is an exact eigenvector of A, whatever the rounding
@@ -413,6 +429,145 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     if (is_fp64 || inv_failed) out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
 #endif
     out.status = inv_failed ? PLK_PX_EVD : (!conv ? PLK_PX_NOCONV : (is_fp64 ? PLK_PX_EMI_FP64 : PLK_PX_EMI));
+    return out;
+}
+
+// Double-precision re-solve, mixed: the quantities the answer depends on are
+// formed in double precision -- the coherence row (from `load`), G^{-1} and
+// A = G^{-1} o C, the residual A x - rho x and rho -- while the shifted
+// inverse B^{-1} is formed and applied in single precision as a
+// preconditioner.  The single-precision inverse iteration (with the same
+// shift refinement) converges first; then x <- x - B^{-1}(A x - rho x) runs in
+// double precision until the correction vanishes, so the fixed point is an
+// eigenvector of the double-precision A (preconditioned inverse iteration).
+// The inversion of G fails (EVD fallback, power iteration on C in double)
+// when a double-precision pivot is <= 1e-12.
+template <int NP, class Loader>
+__device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref, const EmiParams &prm,
+                                       cpx<double> *dbuf, unsigned gmask, int glane0) {
+    PixelResult out;
+    out.flag = false;
+    const bool live = r < n;
+    cpx<float> *fbuf = reinterpret_cast<cpx<float> *>(dbuf);
+
+    cpx<double> A[NP];
+    load_crow<NP, double>(A, load, r, n);
+    double g[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        double m = sqrt(norm2(A[k]));
+        if (prm.beta != 0.f) m = (1.0 - (double)prm.beta) * m + ((k == r) ? (double)prm.beta : 0.0);
+        g[k] = m;
+    }
+    const double minpiv = gj_invert<NP, double, double, true>(g, reinterpret_cast<double *>(dbuf), r, n, gmask);
+    double gs = 0.0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) gs += fabs(g[k]);
+    const bool inv_failed = !(minpiv > Lim<double>::piv_fail) || !isfinite(group_max<NP, double>(gs, gmask));
+
+    cpx<double> x64;
+    double lam = 0.0;
+    bool conv = false;
+    const double tol64 = 1e-9;
+    if (inv_failed) {
+        // EVD fallback: power iteration on C (in A) in double precision.
+        const cpx<double> c0 = live ? load(0) : mk<double>(0.0, 0.0);
+        const double m2 = norm2(c0);
+        x64 = (m2 > 0.0) ? (rsqrt(m2) * c0) : mk<double>(1.0, 0.0);
+        x64 = live ? (rsqrt((double)n) * x64) : mk<double>(0.0, 0.0);
+        double mu_unused = 0.0, q_unused = 0.0;
+        cpx<double> d;
+        auto noreform = [&](double) { return 1.0; };
+        conv = inverse_iteration<NP, double>(A, x64, d, mu_unused, q_unused, noreform, false, dbuf, r, live, gmask,
+                                             1e-9, prm.max_iter);
+        lam = d.x;
+    } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) A[k] = mk<double>(g[k] * A[k].x, g[k] * A[k].y);
+        cpx<float> B[NP];
+        auto formB = [&](float m) {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                B[k] = mk<float>((float)A[k].x, (float)A[k].y);
+                if (k == r) B[k].x -= m;
+            }
+            return gj_invert<NP, float, cpx<float>, false>(B, fbuf, r, n, gmask);
+        };
+        float mu = prm.mu;
+        formB(mu);
+        cpx<float> x;
+        {
+            const cpx<double> c0 = live ? load(0) : mk<double>(0.0, 0.0);
+            const double m2 = norm2(c0);
+            const cpx<double> u = (m2 > 0.0) ? (rsqrt(m2) * c0) : mk<double>(1.0, 0.0);
+            x = live ? mk<float>((float)(u.x * rsqrt((double)n)), (float)(u.y * rsqrt((double)n)))
+                     : mk<float>(0.f, 0.f);
+        }
+        cpx<float> d;
+        float q;
+        inverse_iteration<NP, float>(B, x, d, mu, q, formB, true, fbuf, r, live, gmask, 1e-6f, prm.max_iter);
+        // Tighten the preconditioner for the double-precision phase: shift to
+        // just under lambda_min (by a tenth of the gap measured through q, at
+        // most half the current distance), kept only if B stays positive
+        // definite.  The correction then contracts by about the new ratio
+        // (lambda_min - mu)/(lambda_2 - mu) per step.
+        {
+            const float theta = 1.f / ((d.x != 0.f) ? d.x : 1e-30f);  // lambda_min - mu
+            const float gap = (q > 0.f) ? theta * (1.f / q - 1.f) : 10.f * theta;
+            const float step = fminf(0.5f * theta, 0.1f * gap);
+            if (theta > 0.f && step > 0.f) {
+                const float mu_new = mu + (theta - step);
+                if (formB(mu_new) > 0.f) mu = mu_new;
+                else formB(mu);
+            }
+        }
+        x64 = mk<double>((double)x.x, (double)x.y);
+        double rho = 0.0;
+        for (int it = 0; it < 50; ++it) {
+            const cpx<double> ax = group_matvec<NP, double>(A, x64, dbuf, r, gmask);
+            rho = group_sum<NP, double>(live ? (x64.x * ax.x + x64.y * ax.y) : 0.0, gmask);
+            const cpx<double> res = live ? (ax - rho * x64) : mk<double>(0.0, 0.0);
+            const cpx<float> corr = group_matvec<NP, float>(B, mk<float>((float)res.x, (float)res.y), fbuf, r, gmask);
+            const cpx<double> xn = live ? (x64 - mk<double>((double)corr.x, (double)corr.y)) : mk<double>(0.0, 0.0);
+            const double s2 = group_sum<NP, double>(norm2(xn), gmask);
+            const double c2 = group_sum<NP, double>(live ? (double)norm2(corr) : 0.0, gmask);
+            if (s2 > 0.0) x64 = rsqrt(s2) * xn;
+            if (c2 <= tol64 * tol64) {
+                conv = true;
+                break;
+            }
+        }
+        lam = rho;
+    }
+
+    // Reference and gamma_t (single precision from the double iterate).
+    cpx<double> vr;
+    vr.x = __shfl_sync(gmask, x64.x, glane0 + ref);
+    vr.y = __shfl_sync(gmask, x64.y, glane0 + ref);
+    const cpx<double> w = x64 * conj(vr);
+    float ph = atan2f((float)w.y, (float)w.x);
+    if (r == ref || !live) ph = 0.f;
+    const double wm2 = norm2(w);
+    cpx<float> zeta = (wm2 > 0.0) ? mk<float>((float)(w.x * rsqrt(wm2)), (float)(w.y * rsqrt(wm2)))
+                                  : mk<float>(1.f, 0.f);
+    if (r == ref) zeta = mk<float>(1.f, 0.f);
+    cpx<float> u[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const cpx<double> ck = (live && k < n) ? load(k) : mk<double>(0.0, 0.0);
+        const double m2 = norm2(ck);
+        const cpx<float> uk = (m2 > 0.0) ? mk<float>((float)(ck.x * rsqrt(m2)), (float)(ck.y * rsqrt(m2)))
+                                         : mk<float>(1.f, 0.f);
+        u[k] = (k > r && k < n) ? uk : mk<float>(0.f, 0.f);
+    }
+    const cpx<float> rowsum = group_matvec<NP, float>(u, zeta, fbuf, r, gmask);
+    const cpx<float> term = live ? (conj(zeta) * rowsum) : mk<float>(0.f, 0.f);
+    const float sx = group_sum<NP, float>(term.x, gmask);
+    const float sy = group_sum<NP, float>(term.y, gmask);
+    out.phase = ph;
+    out.tcoh = sqrtf(sx * sx + sy * sy) / (0.5f * (float)n * (float)(n - 1));
+    out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
+    out.status = inv_failed ? PLK_PX_EVD : (conv ? PLK_PX_EMI_FP64 : PLK_PX_NOCONV);
     return out;
 }
 

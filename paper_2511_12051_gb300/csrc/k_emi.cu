@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restri
             if (mine >= 0) {
                 const long long p = base + mine;
                 PackedRow<double> ld{C + p * nt, n, r};
-                const PixelResult res =
-                    emi_solve<NP, double>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0, true);
+                const PixelResult res = emi_solve_mixed<NP>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0);
                 if (r < n) phase[(long long)r * npx + p] = res.phase;
                 if (r == 0) {
                     if (tcoh) tcoh[p] = res.tcoh;
@@ -218,7 +217,7 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
                     }
                 }
                 __syncwarp(gmask);
-                const PixelResult res = emi_solve<NP, double>(row, r, n, ref, prm, buf, gmask, glane0, true);
+                const PixelResult res = emi_solve_mixed<NP>(row, r, n, ref, prm, buf, gmask, glane0);
                 if (r < n) phase[(long long)r * npx + p] = res.phase;
                 if (r == 0) {
                     if (tcoh) tcoh[p] = res.tcoh;
