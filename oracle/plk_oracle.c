@@ -39,6 +39,11 @@
 
 typedef double complex cplx;
 
+/* Sec. III-B: "at pixels where the inversion of Gamma-hat fails due to numerical
+ * issues".  Read as: a Cholesky pivot of the unit-diagonal G = |C| at or below
+ * this value. */
+#define ORC_PIVOT_FAIL 1e-4
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
@@ -393,7 +398,9 @@ double orc_temporal_coherence(int N, const double *Cpacked, const double *phihat
 /* S4-S6. Phase linking (Sec. III-B, eq. (emi-eigenvalue-problem)).         */
 /* Per pixel, from the coherence C:                                         */
 /*   G = (1 - beta)|C| + beta I   (beta = 0 is the paper's plug-in |C|)     */
-/*   Cholesky of G; a pivot <= 1e-12 means the inversion fails and the EVD  */
+/*   Cholesky of G; a pivot <= 1e-4 (G has unit diagonal) means the        */
+/*   inversion fails -- G is indefinite, which |C| of a highly coherent C    */
+/*   often is, or too close to singular to invert reliably -- and the EVD    */
 /*   fallback is used: v = eigenvector of the largest eigenvalue of C       */
 /*   (status 2).  Otherwise A = G^{-1} o C (Hadamard) and v = eigenvector  */
 /*   of the smallest eigenvalue of A (status 0), from a full Jacobi         */
@@ -451,7 +458,7 @@ void orc_phase_link(const double *Cpacked, int N, long npx, int ref, double beta
                 free(ga);
             }
             double l, g;
-            if (cholesky(N, G, L, 1e-12) == 0) {
+            if (cholesky(N, G, L, ORC_PIVOT_FAIL) == 0) {
                 cholesky_inverse(N, L, Gi);
                 for (int i = 0; i < N; ++i)
                     for (int k = 0; k < N; ++k) A[i * N + k] = Gi[i * N + k] * C[i * N + k];

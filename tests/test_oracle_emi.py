@@ -298,3 +298,16 @@ def test_compress_no_data_cell_is_zero():
     ph[:, 1, 2] = np.nan
     k = oracle.compress(z, 0, (1, 1, 1, 1), ph)
     assert k[1, 2] == 0 and np.all(k[0] != 0)
+
+
+def test_inversion_failure_threshold():
+    # Sec. III-B's "inversion fails due to numerical issues", read as a Cholesky
+    # pivot of the unit-diagonal |C| at or below 1e-4: for N=2 the second pivot is
+    # exactly 1 - g^2.  Both answers have the interferogram phase for N=2; the
+    # status tells which branch ran.
+    for pivot, want in ((2e-4, 0), (1.5e-4, 0), (5e-5, 2), (0.0, 2)):
+        g = np.sqrt(1.0 - pivot)
+        C = np.array([[1.0, g * np.exp(0.3j), 1.0]])
+        out = oracle.phase_link(C, 2, ref=0)
+        assert out["status"][0] == want, (pivot, out["status"][0])
+        assert abs(wrapped(out["phase"][1, 0] + 0.3)) < 1e-9
