@@ -92,12 +92,18 @@ typedef struct plk_state plk_state;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out is owned by the
- * caller and released with plk_destroy.  Errors: EINVAL (null out, bad
+ * caller and released with plk_destroy; it holds an 8-byte device counter
+ * (allocated here, the only allocation of a context).  Errors: EINVAL (null out, bad
  * device), ENOMEM, ECUDA. */
 plk_status plk_create(plk_ctx **out, int device, void *cuda_stream);
 plk_status plk_destroy(plk_ctx *ctx);
 /* Switch the stream used by later calls. */
 plk_status plk_set_stream(plk_ctx *ctx, void *cuda_stream);
+/* Wait for the work issued on ctx's stream.  Returns PLK_ETIMEOUT if a
+ * bounded device-side wait (a kernel waiting for its staged tile data) gave up
+ * since the last plk_sync -- that launch's outputs are then incomplete --
+ * else PLK_ECUDA on an asynchronous CUDA error, else PLK_OK. */
+plk_status plk_sync(plk_ctx *ctx);
 /* Text of the last error on this context (static storage owned by ctx). */
 const char *plk_last_error(const plk_ctx *ctx);
 /* Fill *p with the defaults listed in plk_params. */

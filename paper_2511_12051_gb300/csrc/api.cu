@@ -13,6 +13,7 @@
 struct plk_ctx {
     int device;
     cudaStream_t stream;
+    unsigned long long *work;  // device counter of the FP64 re-solve
     char err[512];
     plk::Prof prof;
     // aggregated by plk_profile_collect
@@ -184,17 +185,38 @@ plk_status plk_create(plk_ctx **out, int device, void *cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->err[0] = 0;
     ctx->n_agg = 0;
+    ctx->work = nullptr;
+    {
+        DeviceGuard dg(device);
+        if (cudaMalloc(&ctx->work, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return fail(nullptr, PLK_ENOMEM, "plk_create: device allocation failed");
+        }
+    }
     *out = ctx;
     return PLK_OK;
 }
 
 plk_status plk_destroy(plk_ctx *ctx) {
     if (!ctx) return PLK_OK;
-    if (ctx->prof.ev[0]) {
+    {
         DeviceGuard dg(ctx->device);
-        for (int i = 0; i < 2 * plk::Prof::kMaxRecords; ++i) cudaEventDestroy(ctx->prof.ev[i]);
+        if (ctx->prof.ev[0])
+            for (int i = 0; i < 2 * plk::Prof::kMaxRecords; ++i) cudaEventDestroy(ctx->prof.ev[i]);
+        cudaFree(ctx->work);
     }
     delete ctx;
+    return PLK_OK;
+}
+
+plk_status plk_sync(plk_ctx *ctx) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_sync: null ctx");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_sync");
+    if (plk::read_and_clear_wait_timeout())
+        return fail(ctx, PLK_ETIMEOUT, "plk_sync: a device-side wait for staged tile data gave up");
     return PLK_OK;
 }
 
@@ -323,6 +345,7 @@ plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int 
 }
 
 static plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha) {
+    out->work = ctx->work;
     plk_params p;
     if (params) p = *params;
     else plk_default_params(&p);

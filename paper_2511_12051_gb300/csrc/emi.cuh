@@ -28,17 +28,22 @@ namespace plk {
 
 template <class T> struct Lim;
 template <> struct Lim<float> {
-    static constexpr float piv_flag = 1e-6f;  // G pivot below: hand the pixel to the FP64 path
-    static constexpr float piv_fail = 1e-6f;  // G pivot below: inversion failed (FP32-only mode)
     static constexpr float tiny = 1e-30f;
     static constexpr float big = 3.0e38f;
 };
 template <> struct Lim<double> {
-    static constexpr double piv_flag = 0.0;
-    static constexpr double piv_fail = 1e-12;  // the Cholesky pivot limit of the FP64 reference
     static constexpr double tiny = 1e-300;
     static constexpr double big = 1e300;
 };
+
+// The inversion of G fails (EVD fallback, Sec. III-B) when its Cholesky
+// factorisation meets a pivot <= kPivotFail (G has unit diagonal): G is
+// indefinite, as |C| of a highly coherent C often is, or too close to
+// singular.  The Gauss-Jordan pivots are the same Schur complements.  In
+// single precision a pivot within kPivotBand of the limit is left to the
+// double-precision path (about 0.05% of pixels on burst-shaped stacks).
+constexpr double kPivotFail = 1e-4;
+constexpr double kPivotBand = 2e-5;
 
 template <int NP, class T>
 __device__ __forceinline__ T group_sum(T v, unsigned gmask) {
@@ -100,19 +105,29 @@ __device__ __forceinline__ cpx<T> real_s(cpx<T>, T v) { return mk<T>(v, T(0)); }
 // leave the n x n block untouched.
 // PD = true (real G): pivots are expected positive; a pivot <= tiny is
 // replaced by tiny.  PD = false (complex B, possibly indefinite): only a pivot
-// of magnitude below tiny is replaced.  Returns, in every lane, the smallest
-// real pivot met over the first n steps (before replacement).
+// of magnitude below tiny is replaced.  Returns, in every lane, the first real
+// pivot (in step order, over the first n steps, before replacement) that is
+// <= thr -- the one a Cholesky factorisation would stop at -- or, if there is
+// none, the smallest pivot.
 template <int NP, class T, class S, bool PD>
-__device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigned gmask) {
+__device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigned gmask, T thr) {
     constexpr int E = 16 / sizeof(S);
     static_assert(NP % E == 0, "row must be a multiple of 16 bytes");
     T minpiv = Lim<T>::big;
+    T first_low = Lim<T>::big;
+    int first_step = NP;
 #pragma unroll 1
     for (int k = 0; k < NP; ++k) {
         if (r == k) {
             S piv = a[0];
             const T pr = re_s(piv);
-            if (k < n) minpiv = fmin(minpiv, pr);
+            if (k < n) {
+                minpiv = fmin(minpiv, pr);
+                if (pr <= thr && k < first_step) {
+                    first_step = k;
+                    first_low = pr;
+                }
+            }
             if (PD) {
                 if (!(pr > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
             } else {
@@ -146,7 +161,18 @@ __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigne
         a[NP - 1] = last;
         __syncwarp(gmask);
     }
-    return group_min<NP, T>(minpiv, gmask);
+    // The lane holding the earliest low pivot wins (each pivot lives in one lane).
+    int step = first_step;
+#pragma unroll
+    for (int off = NP / 2; off >= 1; off >>= 1) {
+        const int os = __shfl_xor_sync(gmask, step, off);
+        const T ov = __shfl_xor_sync(gmask, first_low, off);
+        if (os < step) {
+            step = os;
+            first_low = ov;
+        }
+    }
+    return (step < NP) ? first_low : group_min<NP, T>(minpiv, gmask);
 }
 
 // y = sum_j a[j] * v_j where v (one entry per lane) is published in buf.
@@ -208,7 +234,7 @@ __device__ __forceinline__ T form_shift_inverse(cpx<T> (&a)[NP], const T (&g)[NP
         a[k] = mk<T>(g[k] * a[k].x, g[k] * a[k].y);
         if (k == r) a[k].x -= mu;
     }
-    return gj_invert<NP, T, cpx<T>, false>(a, cbuf, r, n, gmask);
+    return gj_invert<NP, T, cpx<T>, false>(a, cbuf, r, n, gmask, T(0));
 }
 
 // y = A x with A = G^{-1} o C, row r from g and the reloaded C row.
@@ -306,43 +332,46 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
 
     // G = (1 - beta)|C| + beta I, and its inverse (kept in g).
     T g[NP];
-    T rs = 0;
+    T rs = 0, mmin = T(1);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        T m = sqrt_t(norm2(a[k]));
+        const T mc = sqrt_t(norm2(a[k]));
+        if (k != r && k < n && live) mmin = fmin(mmin, mc);
+        T m = mc;
         if (prm.beta != 0.f) m = (T(1) - T(prm.beta)) * m + ((k == r) ? T(prm.beta) : T(0));
         g[k] = m;
         rs += abs_t(m);
     }
-    const T norm_g = group_max<NP, T>(live ? rs : T(0), gmask);
-    const T minpiv = gj_invert<NP, T, T, true>(g, rbuf, r, n, gmask);
-    T rsi = 0;
-#pragma unroll
-    for (int k = 0; k < NP; ++k) rsi += abs_t(g[k]);
-    const T norm_gi = group_max<NP, T>(live ? rsi : T(0), gmask);
-    const T cond = norm_g * norm_gi;
-    const bool finite = isfinite(cond);
-
     // Rank one (a single look, e.g. an isolated persistent scatterer): every
-    // |C_ik| is 1 to rounding, G is singular, and the EVD fallback's answer is
-    // exact in single precision.  Any other singular-looking G goes to the
-    // double-precision path, which applies the reference pivot limit.
-    bool rank_one = false;
-    if (!is_fp64 && (minpiv <= Lim<T>::piv_flag || !finite)) {
-        T mmin = T(1);
-        load_crow<NP, T>(a, load, r, n);
+    // |C_ik| is 1 up to the rounding of the products and reciprocal square roots
+    // that normalise it (a few ulps each); G is singular, the EVD fallback
+    // applies and its answer (the phases of column 0) is exact in single
+    // precision.  Any other singular-looking G goes to double precision, which
+    // applies the reference pivot limit.
+    const bool rank_one = !is_fp64 && prm.beta == 0.f && group_min<NP, T>(mmin, gmask) >= T(1) - T(64) * Eps<T>::v;
+    const T norm_g = group_max<NP, T>(live ? rs : T(0), gmask);
+    T minpiv = T(1), cond = T(1), norm_gi = T(1);
+    bool finite = true;
+    const T pfail = T(kPivotFail), pband = is_fp64 ? T(0) : T(kPivotBand);
+    if (!rank_one) {
+        minpiv = gj_invert<NP, T, T, true>(g, rbuf, r, n, gmask, pfail + pband);
+        T rsi = 0;
 #pragma unroll
-        for (int k = 0; k < NP; ++k) mmin = fmin(mmin, sqrt_t(norm2(a[k])) + ((k == r || k >= n || !live) ? T(1) : T(0)));
-        // |C_ik| of a single look is 1 up to the rounding of the products and
-        // reciprocal square roots that normalise it (a few ulps each).
-        rank_one = group_min<NP, T>(mmin, gmask) >= T(1) - T(64) * Eps<T>::v;
+        for (int k = 0; k < NP; ++k) rsi += abs_t(g[k]);
+        norm_gi = group_max<NP, T>(live ? rsi : T(0), gmask);
+        cond = norm_g * norm_gi;
+        finite = isfinite(cond);
     }
-    if (!is_fp64 && prm.fp64_resolve && !rank_one &&
-        (minpiv <= Lim<T>::piv_flag || !finite || cond > T(prm.cond_max))) {
+    // Decision: a pivot clearly below the limit fails, one clearly above
+    // passes; a pivot inside the band (or a non-finite inverse without a clear
+    // failure) is decided in double precision.
+    const bool clear_fail = rank_one || minpiv <= pfail - pband;
+    const bool ambiguous = !clear_fail && (minpiv <= pfail + pband || !finite);
+    if (!is_fp64 && prm.fp64_resolve && !clear_fail && (ambiguous || cond > T(prm.cond_max))) {
         out.flag = true;
         return out;
     }
-    const bool inv_failed = rank_one || (minpiv <= Lim<T>::piv_fail) || !finite;
+    const bool inv_failed = clear_fail || (minpiv <= pfail) || !finite;
 
     T mu = T(prm.mu);
     if (inv_failed) {
@@ -459,11 +488,12 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
         if (prm.beta != 0.f) m = (1.0 - (double)prm.beta) * m + ((k == r) ? (double)prm.beta : 0.0);
         g[k] = m;
     }
-    const double minpiv = gj_invert<NP, double, double, true>(g, reinterpret_cast<double *>(dbuf), r, n, gmask);
+    const double minpiv =
+        gj_invert<NP, double, double, true>(g, reinterpret_cast<double *>(dbuf), r, n, gmask, kPivotFail);
     double gs = 0.0;
 #pragma unroll
     for (int k = 0; k < NP; ++k) gs += fabs(g[k]);
-    const bool inv_failed = !(minpiv > Lim<double>::piv_fail) || !isfinite(group_max<NP, double>(gs, gmask));
+    const bool inv_failed = !(minpiv > kPivotFail) || !isfinite(group_max<NP, double>(gs, gmask));
 
     cpx<double> x64;
     double lam = 0.0;
@@ -491,7 +521,7 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
                 B[k] = mk<float>((float)A[k].x, (float)A[k].y);
                 if (k == r) B[k].x -= m;
             }
-            return gj_invert<NP, float, cpx<float>, false>(B, fbuf, r, n, gmask);
+            return gj_invert<NP, float, cpx<float>, false>(B, fbuf, r, n, gmask, 0.f);
         };
         float mu = prm.mu;
         formB(mu);

@@ -19,6 +19,19 @@ struct PackedRow {
 };
 
 constexpr int kEmiWarps = 4;
+
+// Work counter of the double-precision re-solve (one per context): warps take
+// 32-pixel chunks of the status array in turn, so the few long-running pending
+// pixels spread over all resident warps instead of waiting for the chunks
+// statically assigned to them.  Reset by k_reset_counter before each re-solve
+// launch (stream order).
+__global__ void k_reset_counter(unsigned long long *c) { *c = 0; }
+
+__device__ __forceinline__ long long next_chunk(unsigned long long *counter, int lane) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(counter, 1ull);
+    return (long long)__shfl_sync(0xffffffffu, c, 0);
+}
 // CTAs per SM the single-precision kernel is register-budgeted for (NP <= 16).
 #ifndef PLK_EMI_MINB
 #define PLK_EMI_MINB 4
@@ -87,9 +100,9 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restri
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
-    const long long step = (long long)gridDim.x * kEmiWarps * 32;
-
-    for (long long base = ((long long)blockIdx.x * kEmiWarps + warp) * 32; base < npx; base += step) {
+    for (;;) {
+        const long long base = next_chunk(prm.work, lane) * 32;
+        if (base >= npx) break;
         const long long pl = base + lane;
         const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
         unsigned bal = __ballot_sync(0xffffffffu, pend);
@@ -145,9 +158,9 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
     const int grp = lane / NP, r = lane - grp * NP;
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
-    const long long step = (long long)gridDim.x * kEmiWarps * 32;
-
-    for (long long base = ((long long)blockIdx.x * kEmiWarps + warp) * 32; base < npx; base += step) {
+    for (;;) {
+        const long long base = next_chunk(prm.work, lane) * 32;
+        if (base >= npx) break;
         const long long pl = base + lane;
         const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
         unsigned bal = __ballot_sync(0xffffffffu, pend);
@@ -244,8 +257,10 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
     if (prof) prof->end(s);
     if (e != cudaSuccess || !prm.fp64_resolve) return e;
     long long blocks64 = ((npx + 31) / 32 + kEmiWarps - 1) / kEmiWarps;
-    blocks64 = blocks64 > cap ? cap : (blocks64 < 1 ? 1 : blocks64);
+    const long long cap64 = (long long)device_sm_count() * 2;  // resident CTAs at this kernel's register use
+    blocks64 = blocks64 > cap64 ? cap64 : (blocks64 < 1 ? 1 : blocks64);
     if (prof) prof->begin("phase_link_fp64", s);
+    k_reset_counter<<<1, 1, 0, s>>>(prm.work);
     if (src)
         k_emi64_stack<NP><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(*src->z, *src->g, src->mask, n, npx, ref, prm,
                                                                         phase, tcoh, lam, status);

@@ -44,12 +44,13 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
         (shp_count && ((uintptr_t)shp_count % 2)))
         return fail(PLK_EINVAL, "plk_phase_link_stack_noalloc: misaligned pointer");
 
-    // Scratch layout: sums [H][W] float | mask [Ho][Wo][words] | counts | C.
+    // Scratch layout: work counter | sums [H][W] float | mask [Ho][Wo][words] | counts | C.
+    const size_t b_work = 256;
     const size_t b_pow = align256((size_t)npix * sizeof(float));
     const size_t b_mask = align256((size_t)nout * g.nwords * sizeof(uint64_t));
     const size_t b_cnt = align256((size_t)nout * sizeof(uint16_t));
     const size_t b_c = align256((size_t)nout * plk::ntri(N) * sizeof(float2));
-    const size_t need = b_pow + b_mask + b_cnt + b_c;
+    const size_t need = b_work + b_pow + b_mask + b_cnt + b_c;
     if (need > (size_t)PLK_NOALLOC_SCRATCH_BYTES) {
         char msg[256];
         snprintf(msg, sizeof msg,
@@ -79,6 +80,8 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
         g_scratch_addr[dev] = addr;
     }
     unsigned char *base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(base);
+    base += b_work;
     float *sum_pow = reinterpret_cast<float *>(base);
     uint64_t *mask = reinterpret_cast<uint64_t *>(base + b_pow);
     uint16_t *cnt = shp_count ? shp_count : reinterpret_cast<uint16_t *>(base + b_pow + b_mask);
@@ -93,6 +96,7 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
     prm.err_max = p.err_max;
     prm.max_iter = p.max_iter;
     prm.fp64_resolve = p.fp64_resolve ? 1 : 0;
+    prm.work = work;
 
     // Every scratch region is written in full before it is read in this call.
     e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(slc), N, npix, sum_pow, nullptr, 0, s);

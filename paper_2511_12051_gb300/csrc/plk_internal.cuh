@@ -38,6 +38,7 @@ struct EmiParams {
     float beta, mu, tol, cond_max, err_max;
     int max_iter;
     int fp64_resolve;
+    unsigned long long *work;  // device work counter of the FP64 re-solve (owned by the caller's context)
 };
 
 __host__ __device__ inline long long ntri(int n) { return (long long)n * (n + 1) / 2; }
@@ -69,6 +70,8 @@ cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &
                             float2 *kappa, cudaStream_t s);
 
 int device_sm_count();
+// Nonzero if a bounded device-side wait gave up since the last call (then cleared).
+int read_and_clear_wait_timeout();
 // Text returned by plk_last_error(NULL) on this thread.
 void set_noctx_error(const char *msg);
 

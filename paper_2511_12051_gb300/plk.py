@@ -52,6 +52,7 @@ _SIGS = {
     "plk_create": [ctypes.POINTER(_P), _I, _P],
     "plk_destroy": [_P],
     "plk_set_stream": [_P, _P],
+    "plk_sync": [_P],
     "plk_default_params": [ctypes.POINTER(Params)],
     "plk_output_shape": [_I, _I, Window, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "plk_glrt_threshold": [ctypes.c_double, _I, ctypes.POINTER(ctypes.c_double)],
@@ -164,6 +165,10 @@ class Context:
         h = ctypes.c_void_p()
         _check(lib().plk_create(ctypes.byref(h), dev.index, ctypes.c_void_p(self.stream.cuda_stream)))
         self.h = h
+
+    def sync(self):
+        """Wait for this context's work; raises on a timed-out device wait."""
+        _check(lib().plk_sync(self.h), self.h)
 
     def set_stream(self, stream: torch.cuda.Stream):
         self.stream = stream
