@@ -263,7 +263,31 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
     q = T(0);
     T dl_prev = T(-1);
     int in_round = 0, reshifts = 0;
-    for (int it = 0; it < max_iter; ++it) {
+    // reform_to > 0: rebuild a[] for shift mu_try before the next step; a
+    // failed inertia check (B not positive definite) rebuilds it once more for
+    // the old shift.  One call site keeps the inlined elimination code single.
+    T mu_try = mu;
+    int pending = 0;  // 0 none, 1 try mu_try, 2 restore mu
+    for (int it = 0; it < max_iter + 2 * 3; ++it) {
+        if (pending) {
+            const T pmin = reform(pending == 1 ? mu_try : mu);
+            if (pending == 1 && pmin > T(0)) {
+                mu = mu_try;
+                ++reshifts;
+                pending = 0;
+            } else if (pending == 1) {
+                reshifts = 3;
+                pending = 2;
+                continue;
+            } else {
+                pending = 0;
+            }
+            in_round = 0;
+            dl_prev = T(-1);
+            q = T(0);
+            continue;
+        }
+        if (it - 2 * reshifts >= max_iter) break;
         cpx<T> y = group_matvec<NP, T>(a, x, cbuf, r, gmask);
         if (!live) y = mk<T>(T(0), T(0));
         const T s = group_sum<NP, T>(norm2(y), gmask);          // |y|^2
@@ -284,17 +308,8 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
             // positive definite (the shift is still below lambda_min),
             // otherwise restore the previous one and stop moving it.
             const T lam_est = mu + T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
-            const T mu_new = mu + T(0.75) * (lam_est - mu);
-            if (reform(mu_new) > T(0)) {
-                mu = mu_new;
-                ++reshifts;
-            } else {
-                reform(mu);
-                reshifts = 3;
-            }
-            in_round = 0;
-            dl_prev = T(-1);
-            q = T(0);
+            mu_try = mu + T(0.75) * (lam_est - mu);
+            pending = 1;
         }
     }
     return false;
