@@ -49,6 +49,16 @@ def measured_peaks() -> dict:
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+# DRAM bytes per output pixel of a launch, from the ncu capture summarised in
+# profiles/k_emi32_k_cov_tma_1024x4096.md (1024x4096 case; traffic grows with
+# the pixel count).  Valid for the kernel versions profiled there: a kernel
+# changed since its capture must drop out of this table (traffic null).
+NCU_DRAM_BYTES_PER_OUTPUT_PX = {
+    "phase_link_fp32": (223.641088e6 + 17.391616e6) / 232562,
+    "covariance": (510.597632e6 + 196.865536e6) / 232562,
+}
+
+
 def flops_covariance(N: int, looks_total: float) -> float:
     """Algorithmic flops of the Hermitian sample covariance: 4 N^2 per look."""
     return 4.0 * N * N * looks_total
@@ -191,9 +201,8 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2511_12051_gb300 import dist as pdist
+    rank, world, local = pdist.rank_info()
 
     if args.impl == "reference":
         return run_reference(args, rank)
@@ -210,7 +219,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     # Each rank processes its own burst (weak scaling; no data-path collective).
-    spec = synth.config_spec(1, seed=1 + rank, H=args.rows, W=args.cols)
+    spec = synth.config_spec(1, seed=pdist.unit_seed(1, rank), H=args.rows, W=args.cols)
     z = synth.generate(spec, device=dev)
     stream = torch.cuda.Stream(dev)
     ctx = plk.Context(dev, stream)
@@ -236,8 +245,7 @@ def main():
     # ---------------------------------------------------------- timed region
     clocks = ClockSampler(local)
     ctx.profile(True)
-    if world > 1:
-        dist.barrier()
+    pdist.barrier()
     torch.cuda.synchronize(dev)
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -252,10 +260,7 @@ def main():
     ms_total = e0.elapsed_time(e1)
     kernels = ctx.profile_collect()
     ctx.profile(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = pdist.max_over_ranks(ms_total, dev)
     ms_step = ms_total / args.steps
     value = npx * world * args.steps / (ms_total / 1e3)
     launches = sum(c for _, c in kernels.values())
@@ -282,7 +287,8 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
     roof["kernel"] = dom_name
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None  # ncu DRAM bytes of the current kernel version: see profiles/
+    per_px = NCU_DRAM_BYTES_PER_OUTPUT_PX.get(dom_name)
+    roof["traffic"] = per_px * npx if (per_px and args.rows == H_FULL and args.cols == W_FULL) else None
     roof["avg_launch_ms"] = dom_ms / dom_n
 
     # ------------------------------------------------------------------ e2e
@@ -303,8 +309,7 @@ def main():
         with torch.cuda.stream(stream):
             e2e_step()
         torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
+        pdist.barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         ne = max(1, min(args.steps, 5))
@@ -314,11 +319,7 @@ def main():
                 e2e_step()
             f1.record(stream)
         torch.cuda.synchronize(dev)
-        ms_e2e = f0.elapsed_time(f1)
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = pdist.max_over_ranks(f0.elapsed_time(f1), dev)
         e2e = {"value": npx * world * ne / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_e2e / ne}
         del zh, oh
@@ -354,7 +355,7 @@ def main():
         }
         print(json.dumps(line), flush=True)
     if world > 1:
-        dist.barrier()
+        pdist.barrier()
         dist.destroy_process_group()
     return 0
 

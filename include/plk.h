@@ -104,6 +104,11 @@ plk_status plk_set_stream(plk_ctx *ctx, void *cuda_stream);
  * since the last plk_sync -- that launch's outputs are then incomplete --
  * else PLK_ECUDA on an asynchronous CUDA error, else PLK_OK. */
 plk_status plk_sync(plk_ctx *ctx);
+/* Failure-detection self-test (not part of the method): launches one warp that
+ * waits on a device barrier nothing will complete.  Its bounded wait gives up
+ * after about a second, so the next plk_sync returns PLK_ETIMEOUT and the
+ * context stays usable.  Faults nothing and hangs nothing. */
+plk_status plk_selftest_bounded_wait(plk_ctx *ctx);
 /* Text of the last error on this context (static storage owned by ctx). */
 const char *plk_last_error(const plk_ctx *ctx);
 /* Fill *p with the defaults listed in plk_params. */

@@ -220,6 +220,14 @@ plk_status plk_sync(plk_ctx *ctx) {
     return PLK_OK;
 }
 
+plk_status plk_selftest_bounded_wait(plk_ctx *ctx) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_selftest_bounded_wait: null ctx");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = plk::launch_wait_selftest(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_selftest_bounded_wait");
+    return PLK_OK;
+}
+
 plk_status plk_profile_enable(plk_ctx *ctx, int enable) {
     if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_profile_enable: null ctx");
     DeviceGuard dg(ctx->device);

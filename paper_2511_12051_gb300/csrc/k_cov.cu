@@ -292,6 +292,24 @@ __global__ void __launch_bounds__(256, 1) k_cov_tma(const __grid_constant__ TmaM
     }
 }
 
+// Diagnostic: one warp waits on an mbarrier that nothing will complete.  The
+// bounded wait gives up after about a second and raises the timeout flag, which
+// plk_sync turns into PLK_ETIMEOUT; the context stays usable.
+__global__ void k_wait_selftest() {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0) && threadIdx.x == 0) atomicOr(&g_wait_timeout, 1);
+}
+
+cudaError_t launch_wait_selftest(cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------- host
 
 int read_and_clear_wait_timeout() {

@@ -72,6 +72,7 @@ cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &
 int device_sm_count();
 // Nonzero if a bounded device-side wait gave up since the last call (then cleared).
 int read_and_clear_wait_timeout();
+cudaError_t launch_wait_selftest(cudaStream_t s);
 // Text returned by plk_last_error(NULL) on this thread.
 void set_noctx_error(const char *msg);
 

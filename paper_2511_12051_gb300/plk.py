@@ -53,6 +53,7 @@ _SIGS = {
     "plk_destroy": [_P],
     "plk_set_stream": [_P, _P],
     "plk_sync": [_P],
+    "plk_selftest_bounded_wait": [_P],
     "plk_default_params": [ctypes.POINTER(Params)],
     "plk_output_shape": [_I, _I, Window, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "plk_glrt_threshold": [ctypes.c_double, _I, ctypes.POINTER(ctypes.c_double)],
