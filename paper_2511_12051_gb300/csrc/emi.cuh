@@ -97,15 +97,19 @@ __device__ __forceinline__ cpx<T> real_s(cpx<T>, T v) { return mk<T>(v, T(0)); }
 // held by lane r of the group.  The step loop is not unrolled, so the pivot
 // column cannot be a runtime register index; instead each lane keeps its row
 // rotated: at step k, a[c] holds column (k + c) mod NP, so the pivot column is
-// always a[0].  Step k: lane k publishes its row divided by the pivot (entry 0
-// replaced by 1/pivot); every lane eliminates with it and shifts its row one
-// place left, the freed slot taking the new inverse column.  After NP steps
-// the rotation is complete and a[c] holds column c of the inverse.  Padded
-// rows/columns (index >= n) are the identity: their steps have pivot 1 and
-// leave the n x n block untouched.
-// PD = true (real G): pivots are expected positive; a pivot <= tiny is
-// replaced by tiny.  PD = false (complex B, possibly indefinite): only a pivot
-// of magnitude below tiny is replaced.  Returns, in every lane, the first real
+// always a[0].  Step k: lane k publishes its row as it stands; every lane
+// reads it, takes the pivot p = row[0], and with f' = a[0]/p updates
+//     a[c-1] <- a[c] - f' row[c]   (c = 1..NP-1),   a[NP-1] <- -f'
+// shifting its row one place left; the pivot lane uses f' = 1 - 1/p, which
+// turns the same update into row[c]/p, and takes 1/p as its new last entry.
+// After NP steps the rotation is complete and a[c] holds column c of the
+// inverse.  Padded rows/columns (index >= n) are the identity: their steps have
+// pivot 1 and leave the n x n block untouched.  The pivot lane's update can
+// lose relative accuracy ~eps*|p| for pivots far above 1 (the complex B only,
+// whose inverse serves as a preconditioner); G has pivots <= 1.
+// PD = true (real G): a pivot <= tiny is replaced by tiny.  PD = false
+// (complex B, possibly indefinite): only a pivot of magnitude below tiny is.
+// Every lane sees every pivot, so all return the same value: the first real
 // pivot (in step order, over the first n steps, before replacement) that is
 // <= thr -- the one a Cholesky factorisation would stop at -- or, if there is
 // none, the smallest pivot.
@@ -115,34 +119,39 @@ __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigne
     static_assert(NP % E == 0, "row must be a multiple of 16 bytes");
     T minpiv = Lim<T>::big;
     T first_low = Lim<T>::big;
-    int first_step = NP;
+    bool have_low = false;
 #pragma unroll 1
     for (int k = 0; k < NP; ++k) {
         if (r == k) {
-            S piv = a[0];
-            const T pr = re_s(piv);
-            if (k < n) {
-                minpiv = fmin(minpiv, pr);
-                if (pr <= thr && k < first_step) {
-                    first_step = k;
-                    first_low = pr;
-                }
-            }
-            if (PD) {
-                if (!(pr > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
-            } else {
-                if (!(abs_t(pr) > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
-            }
-            const S inv = inv_s(piv);
-            buf[0] = inv;
 #pragma unroll
-            for (int c = 1; c < NP; ++c) buf[c] = mul_s(a[c], inv);
+            for (int j = 0; j < NP; ++j) buf[j] = a[j];
         }
         __syncwarp(gmask);
-        const S f = a[0];
         const bool pivot_lane = (r == k);
         const uint4 *src = reinterpret_cast<const uint4 *>(buf);
-        S last;
+        S piv;
+        {
+            const uint4 v0 = src[0];
+            S p0[E];
+            memcpy(p0, &v0, 16);
+            piv = p0[0];
+        }
+        const T pr = re_s(piv);
+        if (k < n) {
+            minpiv = fmin(minpiv, pr);
+            if (!have_low && pr <= thr) {
+                have_low = true;
+                first_low = pr;
+            }
+        }
+        if (PD) {
+            if (!(pr > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
+        } else {
+            if (!(abs_t(pr) > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
+        }
+        const S inv = inv_s(piv);
+        const S one = real_s(piv, T(1));
+        const S fp = pivot_lane ? (one - inv) : mul_s(a[0], inv);
 #pragma unroll
         for (int q = 0; q < NP / E; ++q) {
             const uint4 v = src[q];
@@ -151,28 +160,13 @@ __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigne
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = q * E + e;
-                if (j == 0) {
-                    last = pivot_lane ? p[0] : neg_s(mul_s(f, p[0]));
-                } else {
-                    a[j - 1] = pivot_lane ? p[e] : fms_s(f, p[e], a[j]);
-                }
+                if (j > 0) a[j - 1] = fms_s(fp, p[e], a[j]);
             }
         }
-        a[NP - 1] = last;
+        a[NP - 1] = pivot_lane ? inv : neg_s(fp);
         __syncwarp(gmask);
     }
-    // The lane holding the earliest low pivot wins (each pivot lives in one lane).
-    int step = first_step;
-#pragma unroll
-    for (int off = NP / 2; off >= 1; off >>= 1) {
-        const int os = __shfl_xor_sync(gmask, step, off);
-        const T ov = __shfl_xor_sync(gmask, first_low, off);
-        if (os < step) {
-            step = os;
-            first_low = ov;
-        }
-    }
-    return (step < NP) ? first_low : group_min<NP, T>(minpiv, gmask);
+    return have_low ? first_low : minpiv;
 }
 
 // y = sum_j a[j] * v_j where v (one entry per lane) is published in buf.
@@ -257,7 +251,8 @@ __device__ __forceinline__ cpx<T> apply_A(const T (&g)[NP], const Loader &load, 
 template <int NP, class T, class Reform>
 __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cpx<T> &d, T &mu, T &q,
                                                   const Reform &reform, bool allow_reshift, cpx<T> *cbuf, int r,
-                                                  bool live, unsigned gmask, T tol, int max_iter) {
+                                                  bool live, unsigned gmask, T tol, int max_iter,
+                                                  bool build_first) {
     const T tol2 = tol * tol;
     d = mk<T>(T(1), T(0));
     q = T(0);
@@ -267,7 +262,7 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
     // failed inertia check (B not positive definite) rebuilds it once more for
     // the old shift.  One call site keeps the inlined elimination code single.
     T mu_try = mu;
-    int pending = 0;  // 0 none, 1 try mu_try, 2 restore mu
+    int pending = build_first ? 2 : 0;  // 0 none, 1 try mu_try, 2 (re)build for mu
     for (int it = 0; it < max_iter + 2 * 3; ++it) {
         if (pending) {
             const T pmin = reform(pending == 1 ? mu_try : mu);
@@ -389,11 +384,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     const bool inv_failed = clear_fail || (minpiv <= pfail) || !finite;
 
     T mu = T(prm.mu);
-    if (inv_failed) {
-        load_crow<NP, T>(a, load, r, n);  // EVD fallback: power iteration on C
-    } else {
-        form_shift_inverse<NP, T>(a, g, load, mu, cbuf, r, n, gmask);
-    }
+    if (inv_failed) load_crow<NP, T>(a, load, r, n);  // EVD fallback: power iteration on C
 
     // Start vector: phases of column 0 of C (the interferograms to entry 0).
     cpx<T> x;
@@ -408,7 +399,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     T q;
     auto reform = [&](T m) { return form_shift_inverse<NP, T>(a, g, load, m, cbuf, r, n, gmask); };
     const bool conv = inverse_iteration<NP, T>(a, x, d, mu, q, reform, !inv_failed, cbuf, r, live, gmask, tol,
-                                               prm.max_iter);
+                                               prm.max_iter, !inv_failed);
     if (!inv_failed && conv) {
         // Residual correction against A itself: x <- x - B^{-1} (A x - rho x).
         // Its fixed point is an exact eigenvector of A, whatever the rounding
@@ -524,7 +515,7 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
         cpx<double> d;
         auto noreform = [&](double) { return 1.0; };
         conv = inverse_iteration<NP, double>(A, x64, d, mu_unused, q_unused, noreform, false, dbuf, r, live, gmask,
-                                             1e-9, prm.max_iter);
+                                             1e-9, prm.max_iter, false);
         lam = d.x;
     } else {
 #pragma unroll
@@ -539,7 +530,6 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
             return gj_invert<NP, float, cpx<float>, false>(B, fbuf, r, n, gmask, 0.f);
         };
         float mu = prm.mu;
-        formB(mu);
         cpx<float> x;
         {
             const cpx<double> c0 = live ? load(0) : mk<double>(0.0, 0.0);
@@ -550,7 +540,7 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
         }
         cpx<float> d;
         float q;
-        inverse_iteration<NP, float>(B, x, d, mu, q, formB, true, fbuf, r, live, gmask, 1e-6f, prm.max_iter);
+        inverse_iteration<NP, float>(B, x, d, mu, q, formB, true, fbuf, r, live, gmask, 1e-6f, prm.max_iter, true);
         // Tighten the preconditioner for the double-precision phase: shift to
         // just under lambda_min (by a tenth of the gap measured through q, at
         // most half the current distance), kept only if B stays positive
