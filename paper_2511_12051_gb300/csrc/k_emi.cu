@@ -6,6 +6,14 @@
 
 namespace plk {
 
+// Row of the coherence cached in shared memory (one padded slot per lane),
+// gathered once from the packed triangle and re-read from there.
+template <int NP>
+struct SmemRow {
+    const cpx<float> *row;  // this lane's NP entries
+    __device__ __forceinline__ cpx<float> operator()(int k) const { return row[k]; }
+};
+
 // Row r of the packed Hermitian coherence of one pixel, read from global memory.
 template <class T>
 struct PackedRow {
@@ -45,13 +53,16 @@ __global__ void __launch_bounds__(kEmiWarps * 32, NP == 32 ? 1 : PLK_EMI_MINB) k
                                                           float *__restrict__ phase, float *__restrict__ tcoh,
                                                           float *__restrict__ lam, uint8_t *__restrict__ status) {
     constexpr int G = 32 / NP;
+    constexpr int kRowPitch = NP + 1;  // complex entries per cached row (odd: 8-byte loads spread over banks)
     __shared__ __align__(16) cpx<float> sbuf[kEmiWarps][32];
+    __shared__ __align__(16) cpx<float> rowcache[kEmiWarps * 32 * kRowPitch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / NP, r = lane - grp * NP;
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
     const long long step = (long long)gridDim.x * kEmiWarps * G;
+    cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
 
     for (long long base = ((long long)blockIdx.x * kEmiWarps + warp) * G; base < npx; base += step) {
         const long long p = base + grp;
@@ -61,7 +72,28 @@ __global__ void __launch_bounds__(kEmiWarps * 32, NP == 32 ? 1 : PLK_EMI_MINB) k
         if (valid && r < n) nan = isnan(__ldg(Cpix + packed_index(n, r, r)).x);
         nan = __any_sync(gmask, nan);
         if (valid && !nan) {
-            PackedRow<float> ld{Cpix, n, r};
+            // Gather row r once: entries k >= r are contiguous in the packed
+            // triangle, entries k < r are the conjugates down column r.
+            if (r < n) {
+                const int base_r = r * n - r * (r - 1) / 2 - r;  // + k for k >= r
+                int idx_col = r;                                  // packed index of (k, r), k = 0
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    cpx<float> v = mk<float>(0.f, 0.f);
+                    if (k < n) {
+                        if (k >= r) {
+                            const float2 c = __ldg(Cpix + base_r + k);
+                            v = mk<float>(c.x, c.y);
+                        } else {
+                            const float2 c = __ldg(Cpix + idx_col);
+                            v = mk<float>(c.x, -c.y);
+                            idx_col += n - k - 1;
+                        }
+                    }
+                    myrow[k] = v;
+                }
+            }
+            SmemRow<NP> ld{myrow};
             const PixelResult res = emi_solve<NP, float>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0, false);
             if (res.flag) {
                 if (r == 0) status[p] = (uint8_t)kPending;
