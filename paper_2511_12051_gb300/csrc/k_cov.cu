@@ -10,17 +10,20 @@
 // pointing the row-block loads of a rejected look at a zeroed pad pixel (one
 // select per look), so every lane of the warp runs the same loop.
 //
-// Shared-memory layout for the compute: plane pitch PSc = 1 (mod 16 words of
-// 8 bytes) and row pitch RXc with sy*RXc = 1 (mod 16); a warp's PPW pixels are
-// stacked vertically, so one load instruction touches words
-// (plane + row) mod 16 = (bi*B + r + ty) mod 16 -- distinct for B >= PPW and
-// B*BN <= 16 -- and runs without bank conflicts.
+// Shared-memory layout for the compute: pixel-major, cmp[(row * RXc + col) * S
+// + date] with an odd pixel stride S >= B*BN fixed at compile time, so a lane's
+// B loads of a look are one base address plus immediate offsets.  The row
+// pitch RXc is picked on the host by counting, for the lane pattern above, the
+// 8-byte words that one half-warp's load sends to each of the 16 banks.  A
+// rejected look reads one of 16 zero pixels, the one in the same bank as the
+// look itself, so masks do not add bank traffic.  Lanes past the last pixel
+// slot repeat the last slot's first lanes (same addresses, no extra traffic).
 //
 // Staging: the TMA kernel (k_cov_tma) is persistent (one CTA per SM).  One
 // thread issues one 2D tensor copy per date plane (cp.async.bulk.tensor, out-
 // of-image parts zero-filled) into a 128-byte aligned staging buffer and
-// signals an mbarrier; all threads re-lay the tile into the padded compute
-// buffer, and the staging buffer immediately takes the next tile's copies
+// signals an mbarrier; all threads transpose the tile into the pixel-major
+// compute buffer, and the staging buffer immediately takes the next tile's copies
 // while the warps compute.  Every mbarrier wait is bounded; a wait that gives
 // up sets a device flag (read by plk_sync) and the CTA returns.
 // k_cov_plain loads with ordinary coalesced loads (no alignment needs); it is
@@ -40,7 +43,8 @@ __device__ int g_wait_timeout = 0;
 struct CovLayout {
     int TY, TX;    // output tile
     int RY, RX;    // staged region: rows, columns (columns start on an even image column)
-    int RXc, PSc;  // compute buffer: row pitch, plane pitch (elements); zero pixel at RY*RXc
+    int RXc;       // compute buffer row pitch (pixels)
+    int Z0;        // first of the 16 zero pixels (multiple of 16); Z0 + 16 pixels in all
     int PSs;       // staging plane pitch (elements, multiple of 16 = 128 bytes)
     size_t smem_plain, smem_tma;
 };
@@ -48,17 +52,29 @@ struct CovLayout {
 template <int BN>
 __device__ __forceinline__ int diag_lane(int b) { return b * BN - b * (b - 1) / 2; }
 
-// Accumulate, normalise and store the coherence of the tile's pixels from the
-// compute buffer.  xoff: column of the region's first intended column.
+// Pixel stride of the compute buffer: at least B*BN dates, odd, so that 16
+// consecutive pixels of one date fall in 16 different 8-byte banks.
 template <int B, int BN>
-__device__ __forceinline__ void cov_tile(const float2 *__restrict__ cmp, const int PSc, const int RXc, const int n,
+struct PixStride {
+    static constexpr int value = (B * BN) % 2 ? B * BN : B * BN + 1;
+};
+
+// Accumulate, normalise and store the coherence of the tile's pixels from the
+// pixel-major compute buffer cmp[(row * RXc + col) * S + date].  xoff: column
+// of the region's first intended column.
+template <int B, int BN>
+__device__ __forceinline__ void cov_tile(const float2 *__restrict__ cmp, const int RXc, const int Z0, const int n,
                                          const Geom &g, const uint64_t *__restrict__ mask, float2 *__restrict__ C,
-                                         const int ty0, const int tx0, const int TY, const int TX, const int RY,
-                                         const int xoff) {
+                                         const int ty0, const int tx0, const int TY, const int TX, const int xoff) {
     constexpr int U = BN * (BN + 1) / 2;
     constexpr int PPW = 32 / U;
+    constexpr int S = PixStride<B, BN>::value;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int gslot = lane / U, u = lane - gslot * U;
+    const bool lane_active = lane < PPW * U;
+    // Lanes past the last pixel slot repeat the loads of the last slot's first
+    // lanes (same addresses: broadcast, no extra bank traffic) and store nothing.
+    const int gslot = lane_active ? lane / U : PPW - 1;
+    const int u = lane_active ? lane - gslot * U : lane - PPW * U;
     int bi = 0, bk = 0;
     {
         int t = u;
@@ -69,32 +85,20 @@ __device__ __forceinline__ void cov_tile(const float2 *__restrict__ cmp, const i
             t -= len;
         }
     }
-    const bool lane_active = gslot < PPW;
     const int npx_tile = TY * TX;
-    const int zoff = RY * RXc;  // the zero pixel of every compute plane
-
-    int offi[B], offk[B];
-    bool vi[B], vk[B];
-#pragma unroll
-    for (int r = 0; r < B; ++r) {
-        const int i = bi * B + r, k = bk * B + r;
-        vi[r] = i < n;
-        vk[r] = k < n;
-        offi[r] = (vi[r] ? i : 0) * PSc;
-        offk[r] = (vk[r] ? k : 0) * PSc;
-    }
+    const float2 *cmp_i = cmp + bi * B, *cmp_k = cmp + bk * B;
 
     for (int s0 = warp * PPW; s0 < npx_tile; s0 += nwarps * PPW) {
         const int s_raw = s0 + gslot;
-        // Lanes without a pixel read slot 0's window: every shared-memory
-        // address stays inside the staged region.
         const bool in_tile = lane_active && s_raw < npx_tile;
-        const int s = in_tile ? s_raw : 0;
+        const int s = min(s_raw, npx_tile - 1);        // every address stays inside the region
         const int tx = s / TY, ty = s - (s / TY) * TY;  // slots run down a column
         const int oy = ty0 + ty, ox = tx0 + tx;
-        const bool pix_ok = in_tile && oy < g.Ho && ox < g.Wo;
+        const bool px_exists = oy < g.Ho && ox < g.Wo;
+        const bool pix_ok = in_tile && px_exists;  // this lane stores
         const long long o = (long long)oy * g.Wo + ox;
-        const uint64_t *mw = mask + (pix_ok ? o : 0) * g.nwords;
+        // Repeating lanes read the same mask as the lanes they repeat.
+        const uint32_t *mw = reinterpret_cast<const uint32_t *>(mask + (px_exists ? o : 0) * g.nwords);
 
         cpx<float> acc[B][B];
 #pragma unroll
@@ -102,22 +106,25 @@ __device__ __forceinline__ void cov_tile(const float2 *__restrict__ cmp, const i
 #pragma unroll
             for (int q = 0; q < B; ++q) acc[r][q] = mk<float>(0.f, 0.f);
 
-        const int cyr = ty * g.sy + g.hy, cxr = tx * g.sx + g.hx + xoff;
-        uint64_t word = pix_ok ? __ldg(mw) : 0ull;
-        int b = 0, L = 0;
-        for (int dy = -g.hy; dy <= g.hy; ++dy) {
-            const int rowoff = (cyr + dy) * RXc + cxr;
-            for (int dx = -g.hx; dx <= g.hx; ++dx, ++b) {
-                if ((b & 63) == 0 && b > 0) word = pix_ok ? __ldg(mw + (b >> 6)) : 0ull;
-                const bool on = (word >> (b & 63)) & 1ull;
-                L += on;
-                const int off = rowoff + dx;
-                const int offz = on ? off : zoff;  // rejected look: the row block reads zeros
+        int L = 0;
+        uint32_t m = 0;
+        int b = 0;
+        int off = ty * g.sy * RXc + tx * g.sx + xoff;  // window corner (dy = -hy, dx = -hx)
+        for (int dy = 0; dy < g.wy; ++dy, off += RXc - g.wx) {
+            for (int dx = 0; dx < g.wx; ++dx, ++off, ++b) {
+                if ((b & 31) == 0) {
+                    m = px_exists ? __ldg(mw + (b >> 5)) : 0u;
+                    L += __popc(m);
+                }
+                const bool on = m & 1u;
+                m >>= 1;
+                // A rejected look reads the zero pixel in the same bank.
+                const int offz = on ? off : Z0 + (off & 15);
+                const float2 *pi = cmp_i + offz * S, *pk = cmp_k + off * S;
                 cpx<float> zi[B], zk[B];
 #pragma unroll
                 for (int r = 0; r < B; ++r) {
-                    const float2 a = cmp[offi[r] + offz];
-                    const float2 c = cmp[offk[r] + off];
+                    const float2 a = pi[r], c = pk[r];
                     zi[r] = mk<float>(a.x, a.y);
                     zk[r] = mk<float>(c.x, c.y);
                 }
@@ -164,30 +171,42 @@ __device__ __forceinline__ void cov_tile(const float2 *__restrict__ cmp, const i
     }
 }
 
+// Zero the whole compute buffer (pad dates and the 16 zero pixels stay zero).
+template <int S>
+__device__ __forceinline__ void zero_compute(float2 *cmp, const CovLayout &lay) {
+    const int total = (lay.Z0 + 16) * S;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) cmp[idx] = make_float2(0.f, 0.f);
+}
+
 // ------------------------------------------------------------ plain loads
 
 template <int B, int BN>
 __global__ void __launch_bounds__(256) k_cov_plain(const __grid_constant__ Planes z, int n, const Geom g,
                                                    const uint64_t *__restrict__ mask, float2 *__restrict__ C,
                                                    const CovLayout lay) {
-    extern __shared__ __align__(16) float2 sm[];  // n planes of PSc
+    constexpr int S = PixStride<B, BN>::value;
+    extern __shared__ __align__(16) float2 sm[];  // (Z0 + 16) pixels of S dates
     const int tilesY = (g.Ho + lay.TY - 1) / lay.TY;
     const int ty0 = (int)(blockIdx.x % tilesY) * lay.TY;
     const int tx0 = (int)(blockIdx.x / tilesY) * lay.TX;
     const int y0 = ty0 * g.sy + g.sy / 2 - g.hy;
     const int x0 = tx0 * g.sx + g.sx / 2 - g.hx;
-    const int plane = lay.RY * lay.RX;
-    for (int idx = threadIdx.x; idx < n * plane; idx += blockDim.x) {
-        const int d = idx / plane, rem = idx - d * plane;
-        const int ry = rem / lay.RX, rx = rem - ry * lay.RX;
-        const int y = y0 + ry, x = x0 + rx;
-        float2 v = make_float2(0.f, 0.f);
-        if (y >= 0 && y < g.H && x >= 0 && x < g.W) v = __ldg(z.p[d] + (long long)y * g.W + x);
-        sm[d * lay.PSc + ry * lay.RXc + rx] = v;
-    }
-    for (int d = threadIdx.x; d < n; d += blockDim.x) sm[d * lay.PSc + lay.RY * lay.RXc] = make_float2(0.f, 0.f);
+    zero_compute<S>(sm, lay);
     __syncthreads();
-    cov_tile<B, BN>(sm, lay.PSc, lay.RXc, n, g, mask, C, ty0, tx0, lay.TY, lay.TX, lay.RY, 0);
+    // Warp w fills rows (date d, row ry) w, w + nwarps, ...; lanes run along the row.
+    const int nw = blockDim.x >> 5, ln = threadIdx.x & 31;
+    for (int row = threadIdx.x >> 5; row < n * lay.RY; row += nw) {
+        const int d = row / lay.RY, ry = row - d * lay.RY;
+        const int y = y0 + ry;
+        for (int rx = ln; rx < lay.RX; rx += 32) {
+            const int x = x0 + rx;
+            float2 v = make_float2(0.f, 0.f);
+            if (y >= 0 && y < g.H && x >= 0 && x < g.W) v = __ldg(z.p[d] + (long long)y * g.W + x);
+            sm[(ry * lay.RXc + rx) * S + d] = v;
+        }
+    }
+    __syncthreads();
+    cov_tile<B, BN>(sm, lay.RXc, lay.Z0, n, g, mask, C, ty0, tx0, lay.TY, lay.TX, 0);
 }
 
 // --------------------------------------------------------------- TMA path
@@ -234,12 +253,13 @@ template <int B, int BN>
 __global__ void __launch_bounds__(256, 1) k_cov_tma(const __grid_constant__ TmaMaps tm, int n, const Geom g,
                                                     const uint64_t *__restrict__ mask, float2 *__restrict__ C,
                                                     const CovLayout lay, long long ntiles, int tilesY) {
+    constexpr int S = PixStride<B, BN>::value;
     extern __shared__ __align__(128) unsigned char smraw[];
     // Staging planes must start on 128-byte boundaries: align the base by hand
     // (the allocation carries 128 spare bytes).
     unsigned char *base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);
-    float2 *stg = reinterpret_cast<float2 *>(base);   // n planes of PSs (128-byte aligned)
-    float2 *cmp = stg + (size_t)n * lay.PSs;          // n planes of PSc
+    float2 *stg = reinterpret_cast<float2 *>(base);  // n planes of PSs (128-byte aligned)
+    float2 *cmp = stg + (size_t)n * lay.PSs;         // (Z0 + 16) pixels of S dates
     __shared__ __align__(8) uint64_t bar;
     const unsigned tx_bytes = (unsigned)(n * lay.RY * lay.RX * sizeof(float2));
 
@@ -262,22 +282,62 @@ __global__ void __launch_bounds__(256, 1) k_cov_tma(const __grid_constant__ TmaM
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int d = threadIdx.x; d < n; d += blockDim.x) cmp[(size_t)d * lay.PSc + lay.RY * lay.RXc] = make_float2(0.f, 0.f);
+    zero_compute<S>(cmp, lay);
     __syncthreads();
     long long t = blockIdx.x;
     if (threadIdx.x == 0 && t < ntiles) issue(t);
     unsigned parity = 0;
-    const int plane = lay.RY * lay.RX;
+    const int nrows = n * lay.RY, nw = blockDim.x >> 5, ln = threadIdx.x & 31;
     for (; t < ntiles; t += gridDim.x) {
         if (!mbar_wait_bounded(&bar, parity)) {
             atomicOr(&g_wait_timeout, 1);
             return;
         }
         parity ^= 1u;
-        for (int idx = threadIdx.x; idx < n * plane; idx += blockDim.x) {
-            const int d = idx / plane, rem = idx - d * plane;
-            const int ry = rem / lay.RX, rx = rem - ry * lay.RX;
-            cmp[(size_t)d * lay.PSc + ry * lay.RXc + rx] = stg[(size_t)d * lay.PSs + rem];
+        // Transpose staged rows (date d, row ry) into the pixel-major buffer.
+        // Warp w takes rows w, w + nwarps, ...; four rows per pass, all loads
+        // before the stores.  (d, ry) advance without divisions.
+        {
+            int dr[4], yr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int row = (threadIdx.x >> 5) + u * nw;
+                dr[u] = row / lay.RY;
+                yr[u] = row - dr[u] * lay.RY;
+            }
+            for (int row0 = threadIdx.x >> 5; row0 < nrows; row0 += 4 * nw) {
+                float2 v[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = row0 + u * nw < nrows;
+                    const float2 *src = stg + (size_t)dr[u] * lay.PSs + yr[u] * lay.RX;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int rx = ln + 32 * h;
+                        v[u][h] = (ok && rx < lay.RX) ? src[rx] : make_float2(0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (row0 + u * nw >= nrows) continue;
+                    const float2 *src = stg + (size_t)dr[u] * lay.PSs + yr[u] * lay.RX;
+                    float2 *dst = cmp + (size_t)yr[u] * lay.RXc * S + dr[u];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int rx = ln + 32 * h;
+                        if (rx < lay.RX) dst[rx * S] = v[u][h];
+                    }
+                    for (int rx = ln + 64; rx < lay.RX; rx += 32) dst[rx * S] = src[rx];  // rows over 64 columns
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    yr[u] += 4 * nw;
+                    while (yr[u] >= lay.RY) {
+                        yr[u] -= lay.RY;
+                        ++dr[u];
+                    }
+                }
+            }
         }
         __syncthreads();  // staging consumed, compute buffer ready
         const long long nt = t + gridDim.x;
@@ -287,7 +347,7 @@ __global__ void __launch_bounds__(256, 1) k_cov_tma(const __grid_constant__ TmaM
         }
         int ty0, tx0, x0, y0, xoff;
         origin(t, ty0, tx0, x0, y0, xoff);
-        cov_tile<B, BN>(cmp, lay.PSc, lay.RXc, n, g, mask, C, ty0, tx0, lay.TY, lay.TX, lay.RY, xoff);
+        cov_tile<B, BN>(cmp, lay.RXc, lay.Z0, n, g, mask, C, ty0, tx0, lay.TY, lay.TX, xoff);
         __syncthreads();  // compute buffer free for the next tile
     }
 }
@@ -327,36 +387,79 @@ int read_and_clear_wait_timeout() {
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Row pitch >= rx with sy * pitch = 1 (mod 16) when sy is odd (else odd pitch).
-static int row_pitch(int rx, int sy) {
-    for (int p = rx; p < rx + 32; ++p) {
-        if (sy % 2 == 1) {
-            if ((sy * p) % 16 == 1) return p;
-        } else if (p % 2 == 1) {
-            return p;
+// Shared-memory passes of one warp's two load instructions (row block and
+// column block of a look) in the pixel-major buffer: per half-warp, the
+// largest number of distinct 8-byte words that share one of 16 banks.  The
+// lanes are laid out as in cov_tile; its PPW pixels sit sy * pitch pixels apart.
+static int bank_passes(int B, int BN, int S, int sy, int pitch) {
+    const int U = BN * (BN + 1) / 2, PPW = 32 / U;
+    int lane_slot[32], lane_bi[32], lane_bk[32];
+    for (int lane = 0; lane < 32; ++lane) {
+        int gs = lane / U, u = lane - gs * U;
+        if (gs >= PPW) {
+            gs = PPW - 1;
+            u = lane - PPW * U;
         }
+        int bi = 0, bk = 0, t = u;
+        for (int a = 0; a < BN; ++a) {
+            const int len = BN - a;
+            if (t >= 0 && t < len) { bi = a; bk = a + t; }
+            t -= len;
+        }
+        lane_slot[lane] = gs;
+        lane_bi[lane] = bi;
+        lane_bk[lane] = bk;
     }
-    return rx;
+    int total = 0;
+    for (int which = 0; which < 2; ++which)
+        for (int half = 0; half < 2; ++half) {
+            long long addr[16];
+            int na = 0;
+            for (int l = half * 16; l < half * 16 + 16; ++l) {
+                const long long a =
+                    (long long)lane_slot[l] * sy * pitch * S + (long long)(which ? lane_bk[l] : lane_bi[l]) * B;
+                bool seen = false;
+                for (int j = 0; j < na; ++j) seen = seen || addr[j] == a;
+                if (!seen) addr[na++] = a;
+            }
+            int per_bank[16] = {0}, worst = 0;
+            for (int j = 0; j < na; ++j) worst = std::max(worst, ++per_bank[addr[j] % 16]);
+            total += worst;
+        }
+    return total;
 }
 
-static CovLayout make_layout(int n, const Geom &g, int TY, int TX) {
+// Smallest row pitch >= rx with the fewest bank passes.
+static int row_pitch(int B, int BN, int S, int rx, int sy) {
+    int best = rx, best_cost = 1 << 30;
+    for (int p = rx; p < rx + 16; ++p) {
+        const int c = bank_passes(B, BN, S, sy, p);
+        if (c < best_cost) {
+            best_cost = c;
+            best = p;
+        }
+    }
+    return best;
+}
+
+static CovLayout make_layout(int n, int B, int BN, int S, const Geom &g, int TY, int TX) {
     CovLayout l{};
     l.TY = TY;
     l.TX = TX;
     l.RY = (TY - 1) * g.sy + g.wy;
     l.RX = round_up((TX - 1) * g.sx + g.wx + 1, 2);
-    l.RXc = row_pitch(l.RX, g.sy);
-    l.PSc = l.RY * l.RXc + 1;
-    while (l.PSc % 16 != 1) ++l.PSc;
+    l.RXc = row_pitch(B, BN, S, l.RX, g.sy);
+    l.Z0 = round_up(l.RY * l.RXc, 16);
     l.PSs = round_up(l.RY * l.RX, 16);
-    l.smem_plain = (size_t)n * l.PSc * sizeof(float2);
-    l.smem_tma = (size_t)n * (l.PSs + l.PSc) * sizeof(float2) + 128;
+    l.smem_plain = (size_t)(l.Z0 + 16) * S * sizeof(float2);
+    l.smem_tma = (size_t)n * l.PSs * sizeof(float2) + l.smem_plain + 128;
     return l;
 }
 
 // Tile choice: PPW pixels stacked per warp column, 8 warps, several passes for
-// small strides; the score favours little halo per output pixel.
-static CovLayout choose_layout(int n, const Geom &g, int ppw, size_t budget, bool tma) {
+// small strides; the score favours full warps and little halo per output pixel.
+static CovLayout choose_layout(int n, int B, int BN, int S, const Geom &g, size_t budget, bool tma) {
+    const int ppw = 32 / (BN * (BN + 1) / 2);
     CovLayout best{};
     double best_score = -1.0;
     for (int a = 1; a <= 4; ++a)
@@ -364,7 +467,7 @@ static CovLayout choose_layout(int n, const Geom &g, int ppw, size_t budget, boo
             const int TY = ppw * a;
             const int px = TY * TX;
             if (px > 8 * ppw * 8) continue;
-            CovLayout l = make_layout(n, g, TY, TX);
+            CovLayout l = make_layout(n, B, BN, S, g, TY, TX);
             const size_t sm = tma ? l.smem_tma : l.smem_plain;
             if (sm > budget || l.RX > 256 || l.RY > 256) continue;
             const double halo = (double)(TY * g.sy) * (TX * g.sx) / ((double)l.RY * l.RX);
@@ -398,14 +501,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 template <int B, int BN>
 static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                            cudaStream_t s) {
-    constexpr int U = BN * (BN + 1) / 2;
-    constexpr int PPW = 32 / U;
-    const size_t kMaxSmem = 220 * 1024;
+    constexpr int S = PixStride<B, BN>::value;
+    const size_t kMaxSmem = 226 * 1024;
     bool tma = (g.W % 2 == 0) && tensor_map_encoder() != nullptr;
     for (int d = 0; d < n && tma; ++d) tma = ((uintptr_t)z.p[d] % 16) == 0;
     CovLayout lay{};
     if (tma) {
-        lay = choose_layout(n, g, PPW, kMaxSmem, true);
+        lay = choose_layout(n, B, BN, S, g, kMaxSmem, true);
         tma = lay.TY > 0;
     }
     if (tma) {
@@ -433,10 +535,10 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
             return cudaGetLastError();
         }
     }
-    lay = choose_layout(n, g, PPW, 96 * 1024, false);
-    if (lay.TY == 0) lay = choose_layout(n, g, PPW, kMaxSmem, false);
+    lay = choose_layout(n, B, BN, S, g, 96 * 1024, false);
+    if (lay.TY == 0) lay = choose_layout(n, B, BN, S, g, kMaxSmem, false);
     if (lay.TY == 0) {
-        lay = make_layout(n, g, 1, 1);
+        lay = make_layout(n, B, BN, S, g, 1, 1);
         if (lay.smem_plain > kMaxSmem) return cudaErrorInvalidConfiguration;
     }
     cudaError_t e =
@@ -450,14 +552,14 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
 
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                               cudaStream_t s) {
-    // 3 x 3 block grid (5 pixels per warp) up to N = 18; 5 x 5 (2 per warp) beyond.
+    // 3 x 3 block grid (5 pixels per warp) up to N = 18; 5 x 5 (2 per warp) beyond
+    // (blocks of 5 or more dates: 4-date blocks on a 5 x 5 grid collide in banks).
     if (n <= 3) return run_cov<1, 3>(z, n, g, mask, C, s);
     if (n <= 6) return run_cov<2, 3>(z, n, g, mask, C, s);
     if (n <= 9) return run_cov<3, 3>(z, n, g, mask, C, s);
     if (n <= 12) return run_cov<4, 3>(z, n, g, mask, C, s);
     if (n <= 15) return run_cov<5, 3>(z, n, g, mask, C, s);
     if (n <= 18) return run_cov<6, 3>(z, n, g, mask, C, s);
-    if (n <= 20) return run_cov<4, 5>(z, n, g, mask, C, s);
     if (n <= 25) return run_cov<5, 5>(z, n, g, mask, C, s);
     if (n <= 30) return run_cov<6, 5>(z, n, g, mask, C, s);
     return run_cov<7, 5>(z, n, g, mask, C, s);
