@@ -80,6 +80,22 @@ __device__ __forceinline__ float fms_s(float a, float b, float c) { return c - a
 __device__ __forceinline__ double fms_s(double a, double b, double c) { return c - a * b; }
 template <class T>
 __device__ __forceinline__ cpx<T> fms_s(cpx<T> a, cpx<T> b, cpx<T> c) { return cfms(a, b, c); }
+// |c| from |c|^2: x * rsqrt(x) in single precision (a few ulp, one MUFU
+// operation instead of a correctly rounded square root), sqrt in double.
+__device__ __forceinline__ float mag_t(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
+__device__ __forceinline__ double mag_t(double v) { return sqrt(v); }
+// Reciprocal of a pivot: one approximate MUFU operation in single precision
+// (rcp.approx, at most 1 ulp off), a division in double precision.
+__device__ __forceinline__ float rcp_t(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ double rcp_t(double a) { return 1.0 / a; }
+__device__ __forceinline__ float scale_s(float a, float s) { return a * s; }
+__device__ __forceinline__ double scale_s(double a, double s) { return a * s; }
+template <class T>
+__device__ __forceinline__ cpx<T> scale_s(cpx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
 __device__ __forceinline__ float neg_s(float a) { return -a; }
 __device__ __forceinline__ double neg_s(double a) { return -a; }
 template <class T>
@@ -104,7 +120,9 @@ __device__ __forceinline__ cpx<T> real_s(cpx<T>, T v) { return mk<T>(v, T(0)); }
 // turns the same update into row[c]/p, and takes 1/p as its new last entry.
 // After NP steps the rotation is complete and a[c] holds column c of the
 // inverse.  Padded rows/columns (index >= n) are the identity: their steps have
-// pivot 1 and leave the n x n block untouched.  The pivot lane's update can
+// pivot 1 and f' = 0 on every lane, so they only rotate the rows (no publish,
+// no arithmetic).  The pivot is taken as the real part of row[0] (the matrices
+// inverted here are real symmetric or Hermitian).  The pivot lane's update can
 // lose relative accuracy ~eps*|p| for pivots far above 1 (the complex B only,
 // whose inverse serves as a preconditioner); G has pivots <= 1.
 // PD = true (real G): a pivot <= tiny is replaced by tiny.  PD = false
@@ -122,36 +140,49 @@ __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigne
     bool have_low = false;
 #pragma unroll 1
     for (int k = 0; k < NP; ++k) {
-        if (r == k) {
+        const S zero = real_s(a[0], T(0)), one = real_s(a[0], T(1));
+        if (k >= n) {
+            // Padded pivot (identity row and column): f' = 0 on every lane,
+            // the step only rotates the rows.
 #pragma unroll
-            for (int j = 0; j < NP; ++j) buf[j] = a[j];
+            for (int j = 1; j < NP; ++j) a[j - 1] = a[j];
+            a[NP - 1] = (r == k) ? one : zero;
+            continue;
+        }
+        const bool pivot_lane = (r == k);
+        if (pivot_lane) {
+            uint4 *dst = reinterpret_cast<uint4 *>(buf);
+#pragma unroll
+            for (int q = 0; q < NP / E; ++q) {
+                uint4 v;
+                memcpy(&v, &a[q * E], 16);
+                dst[q] = v;
+            }
         }
         __syncwarp(gmask);
-        const bool pivot_lane = (r == k);
         const uint4 *src = reinterpret_cast<const uint4 *>(buf);
-        S piv;
+        T pr;
         {
             const uint4 v0 = src[0];
             S p0[E];
             memcpy(p0, &v0, 16);
-            piv = p0[0];
+            pr = re_s(p0[0]);
         }
-        const T pr = re_s(piv);
-        if (k < n) {
-            minpiv = fmin(minpiv, pr);
-            if (!have_low && pr <= thr) {
-                have_low = true;
-                first_low = pr;
-            }
+        minpiv = fmin(minpiv, pr);
+        if (!have_low && pr <= thr) {
+            have_low = true;
+            first_low = pr;
         }
+        // The pivots of a Hermitian matrix are real (Schur complements of a
+        // Hermitian matrix are Hermitian); the imaginary part of a computed
+        // complex pivot is rounding noise and is dropped.
         if (PD) {
-            if (!(pr > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
+            if (!(pr > Lim<T>::tiny)) pr = Lim<T>::tiny;
         } else {
-            if (!(abs_t(pr) > Lim<T>::tiny)) piv = real_s(piv, Lim<T>::tiny);
+            if (!(abs_t(pr) > Lim<T>::tiny)) pr = Lim<T>::tiny;
         }
-        const S inv = inv_s(piv);
-        const S one = real_s(piv, T(1));
-        const S fp = pivot_lane ? (one - inv) : mul_s(a[0], inv);
+        const T inv = rcp_t(pr);
+        const S fp = pivot_lane ? real_s(a[0], T(1) - inv) : scale_s(a[0], inv);
 #pragma unroll
         for (int q = 0; q < NP / E; ++q) {
             const uint4 v = src[q];
@@ -163,7 +194,7 @@ __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigne
                 if (j > 0) a[j - 1] = fms_s(fp, p[e], a[j]);
             }
         }
-        a[NP - 1] = pivot_lane ? inv : neg_s(fp);
+        a[NP - 1] = pivot_lane ? real_s(a[0], inv) : neg_s(fp);
         __syncwarp(gmask);
     }
     return have_low ? first_low : minpiv;
@@ -345,7 +376,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     T rs = 0, mmin = T(1);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        const T mc = sqrt_t(norm2(a[k]));
+        const T mc = mag_t(norm2(a[k]));
         if (k != r && k < n && live) mmin = fmin(mmin, mc);
         T m = mc;
         if (prm.beta != 0.f) m = (T(1) - T(prm.beta)) * m + ((k == r) ? T(prm.beta) : T(0));
