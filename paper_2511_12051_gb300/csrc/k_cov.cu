@@ -352,6 +352,65 @@ __global__ void __launch_bounds__(256, 1) k_cov_tma(const __grid_constant__ TmaM
     }
 }
 
+// ---------------------------------------------------------- async copies
+
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (the
+// source address is then not read but must still be a valid pointer).
+__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// Persistent kernel, two CTAs per SM: each CTA copies its tile's region
+// straight into the pixel-major compute buffer with per-element asynchronous
+// copies (no staging buffer, no transpose pass), waits for them and computes;
+// while one CTA waits for its copies the other computes.
+template <int B, int BN>
+__global__ void __launch_bounds__(256, 2) k_cov_async(const __grid_constant__ Planes z, int n, const Geom g,
+                                                      const uint64_t *__restrict__ mask, float2 *__restrict__ C,
+                                                      const CovLayout lay, long long ntiles, int tilesY) {
+    constexpr int S = PixStride<B, BN>::value;
+    extern __shared__ __align__(16) float2 sm[];  // (Z0 + 16) pixels of S dates
+    zero_compute<S>(sm, lay);
+    __syncthreads();
+    const int nrows = n * lay.RY, nw = blockDim.x >> 5, ln = threadIdx.x & 31;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ty0 = (int)(t % tilesY) * lay.TY;
+        const int tx0 = (int)(t / tilesY) * lay.TX;
+        const int y0 = ty0 * g.sy + g.sy / 2 - g.hy;
+        const int x0 = tx0 * g.sx + g.sx / 2 - g.hx;
+        const bool x_inside = x0 >= 0 && x0 + lay.RX <= g.W;
+        // Warp w copies rows (date d, row ry) w, w + nwarps, ...; (d, ry)
+        // advance without divisions.
+        int d = (threadIdx.x >> 5) / lay.RY, ry = (threadIdx.x >> 5) - d * lay.RY;
+        for (int row = threadIdx.x >> 5; row < nrows; row += nw) {
+            const int y = y0 + ry;
+            const bool y_inside = y >= 0 && y < g.H;
+            const float2 *plane = z.p[d];
+            const float2 *srow = plane + (long long)(y_inside ? y : 0) * g.W + x0;
+            float2 *drow = sm + (size_t)ry * lay.RXc * S + d;
+            if (y_inside && x_inside) {
+                for (int rx = ln; rx < lay.RX; rx += 32) cp_async8(drow + rx * S, srow + rx, 8);
+            } else {
+                for (int rx = ln; rx < lay.RX; rx += 32) {
+                    const int x = x0 + rx;
+                    const bool ok = y_inside && x >= 0 && x < g.W;
+                    cp_async8(drow + rx * S, ok ? srow + rx : plane, ok ? 8 : 0);
+                }
+            }
+            ry += nw;
+            while (ry >= lay.RY) {
+                ry -= lay.RY;
+                ++d;
+            }
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        __syncthreads();  // every copy of the tile has landed
+        cov_tile<B, BN>(sm, lay.RXc, lay.Z0, n, g, mask, C, ty0, tx0, lay.TY, lay.TX, 0);
+        __syncthreads();  // compute buffer free for the next tile
+    }
+}
+
 // Diagnostic: one warp waits on an mbarrier that nothing will complete.  The
 // bounded wait gives up after about a second and raises the timeout flag, which
 // plk_sync turns into PLK_ETIMEOUT; the context stays usable.
@@ -503,6 +562,30 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
                            cudaStream_t s) {
     constexpr int S = PixStride<B, BN>::value;
     const size_t kMaxSmem = 226 * 1024;
+#ifndef PLK_COV_NO_ASYNC
+    {
+        // Two CTAs per SM: each compute buffer within half the SM's shared
+        // memory (less the per-CTA reservation).
+        const size_t kHalfSm = 113 * 1024;
+        CovLayout la = choose_layout(n, B, BN, S, g, kHalfSm, false);
+        if (la.TY > 0) {
+            cudaError_t e = cudaFuncSetAttribute(k_cov_async<B, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kHalfSm);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cov_async<B, BN>, 256, la.smem_plain);
+            if (e != cudaSuccess) return e;
+            if (per_sm >= 1) {
+                const int tilesY = (g.Ho + la.TY - 1) / la.TY;
+                const long long ntiles = (long long)tilesY * ((g.Wo + la.TX - 1) / la.TX);
+                if (ntiles == 0) return cudaSuccess;
+                const long long grid = std::min<long long>(ntiles, (long long)per_sm * device_sm_count());
+                k_cov_async<B, BN><<<(unsigned)grid, 256, la.smem_plain, s>>>(z, n, g, mask, C, la, ntiles, tilesY);
+                return cudaGetLastError();
+            }
+        }
+    }
+#endif
     bool tma = (g.W % 2 == 0) && tensor_map_encoder() != nullptr;
     for (int d = 0; d < n && tma; ++d) tma = ((uintptr_t)z.p[d] % 16) == 0;
     CovLayout lay{};
