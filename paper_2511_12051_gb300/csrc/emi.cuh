@@ -236,13 +236,23 @@ template <> struct Eps<float> { static constexpr float v = 5.96e-8f; };
 template <> struct Eps<double> { static constexpr double v = 1.11e-16; };
 
 // Row source: `load(k)` returns C_rk (complex, unit diagonal) of this lane's
-// row for k < n; padded entries are produced here.
+// row for k < n; padded entries are produced here.  A source that already
+// holds the padded row (Loader::kPadded) hands it over whole.
+template <class L, class = void>
+struct IsPadded { static constexpr bool value = false; };
+template <class L>
+struct IsPadded<L, decltype(void(L::kPadded))> { static constexpr bool value = L::kPadded; };
+
 template <int NP, class T, class Loader>
 __device__ __forceinline__ void load_crow(cpx<T> (&c)[NP], const Loader &load, int r, int n) {
+    if constexpr (IsPadded<Loader>::value) {
+        load.all(c);
+    } else {
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        if (r < n && k < n) c[k] = load(k);
-        else c[k] = mk<T>((k == r) ? T(1) : T(0), T(0));
+        for (int k = 0; k < NP; ++k) {
+            if (r < n && k < n) c[k] = load(k);
+            else c[k] = mk<T>((k == r) ? T(1) : T(0), T(0));
+        }
     }
 }
 

@@ -59,6 +59,22 @@ struct PixStride {
     static constexpr int value = (B * BN) % 2 ? B * BN : B * BN + 1;
 };
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// B consecutive complex samples from a 32-bit shared address, one 8-byte load
+// each with an immediate offset.
+template <int R>
+__device__ __forceinline__ void lds_one(cpx<float> &v, uint32_t a) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(a), "n"(R * 8));
+}
+template <int B, int R = 0>
+__device__ __forceinline__ void lds_row(cpx<float> (&v)[B], uint32_t a) {
+    if constexpr (R < B) {
+        lds_one<R>(v[R], a);
+        lds_row<B, R + 1>(v, a);
+    }
+}
+
 // Accumulate, normalise and store the coherence of the tile's pixels from the
 // pixel-major compute buffer cmp[(row * RXc + col) * S + date].  xoff: column
 // of the region's first intended column.
@@ -86,7 +102,9 @@ __device__ __forceinline__ void cov_tile(const float2 *__restrict__ cmp, const i
         }
     }
     const int npx_tile = TY * TX;
-    const float2 *cmp_i = cmp + bi * B, *cmp_k = cmp + bk * B;
+    // 32-bit shared addresses of date bi*B (row block) and bk*B (column
+    // block) of pixel 0; a look adds pixel * S * 8 bytes, date r adds 8 r.
+    const uint32_t base_i = smem_addr(cmp) + bi * B * 8, base_k = smem_addr(cmp) + bk * B * 8;
 
     for (int s0 = warp * PPW; s0 < npx_tile; s0 += nwarps * PPW) {
         const int s_raw = s0 + gslot;
@@ -118,16 +136,13 @@ __device__ __forceinline__ void cov_tile(const float2 *__restrict__ cmp, const i
                 }
                 const bool on = m & 1u;
                 m >>= 1;
-                // A rejected look reads the zero pixel in the same bank.
-                const int offz = on ? off : Z0 + (off & 15);
-                const float2 *pi = cmp_i + offz * S, *pk = cmp_k + off * S;
+                // A rejected look reads the zero pixel in the same bank (Z0 is
+                // a multiple of 16).
+                const int offz = on ? off : (Z0 | (off & 15));
+                const uint32_t ai = base_i + (uint32_t)offz * (S * 8), ak = base_k + (uint32_t)off * (S * 8);
                 cpx<float> zi[B], zk[B];
-#pragma unroll
-                for (int r = 0; r < B; ++r) {
-                    const float2 a = pi[r], c = pk[r];
-                    zi[r] = mk<float>(a.x, a.y);
-                    zk[r] = mk<float>(c.x, c.y);
-                }
+                lds_row<B>(zi, ai);
+                lds_row<B>(zk, ak);
 #pragma unroll
                 for (int r = 0; r < B; ++r)
 #pragma unroll

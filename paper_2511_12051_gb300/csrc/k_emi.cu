@@ -6,12 +6,22 @@
 
 namespace plk {
 
-// Row of the coherence cached in shared memory (one padded slot per lane),
-// gathered once from the packed triangle and re-read from there.
+// Row of the coherence cached in shared memory (one slot per lane), gathered
+// once from the packed triangle, already padded (identity rows and zero
+// columns beyond n), and re-read from there with 16-byte loads.
 template <int NP>
 struct SmemRow {
-    const cpx<float> *row;  // this lane's NP entries
+    static constexpr bool kPadded = true;
+    const cpx<float> *row;  // this lane's NP entries, 16-byte aligned
     __device__ __forceinline__ cpx<float> operator()(int k) const { return row[k]; }
+    __device__ __forceinline__ void all(cpx<float> (&c)[NP]) const {
+        const uint4 *src = reinterpret_cast<const uint4 *>(row);
+#pragma unroll
+        for (int q = 0; q < NP / 2; ++q) {
+            const uint4 v = src[q];
+            memcpy(&c[2 * q], &v, 16);
+        }
+    }
 };
 
 // Row r of the packed Hermitian coherence of one pixel, read from global memory.
@@ -53,7 +63,9 @@ __global__ void __launch_bounds__(kEmiWarps * 32, NP == 32 ? 1 : PLK_EMI_MINB) k
                                                           float *__restrict__ phase, float *__restrict__ tcoh,
                                                           float *__restrict__ lam, uint8_t *__restrict__ status) {
     constexpr int G = 32 / NP;
-    constexpr int kRowPitch = NP + 1;  // complex entries per cached row (odd: 8-byte loads spread over banks)
+    // Complex entries per cached row: NP + 2 (16-byte aligned rows whose
+    // 16-byte chunks fall in different banks for 8 consecutive lanes).
+    constexpr int kRowPitch = NP + 2;
     __shared__ __align__(16) cpx<float> sbuf[kEmiWarps][32];
     __shared__ __align__(16) cpx<float> rowcache[kEmiWarps * 32 * kRowPitch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -74,23 +86,30 @@ __global__ void __launch_bounds__(kEmiWarps * 32, NP == 32 ? 1 : PLK_EMI_MINB) k
         if (valid && !nan) {
             // Gather row r once: entries k >= r are contiguous in the packed
             // triangle, entries k < r are the conjugates down column r.
-            if (r < n) {
+            {
                 const int base_r = r * n - r * (r - 1) / 2 - r;  // + k for k >= r
                 int idx_col = r;                                  // packed index of (k, r), k = 0
+                cpx<float> v[NP];
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
-                    cpx<float> v = mk<float>(0.f, 0.f);
-                    if (k < n) {
+                    v[k] = mk<float>((r >= n && k == r) ? 1.f : 0.f, 0.f);
+                    if (r < n && k < n) {
                         if (k >= r) {
                             const float2 c = __ldg(Cpix + base_r + k);
-                            v = mk<float>(c.x, c.y);
+                            v[k] = mk<float>(c.x, c.y);
                         } else {
                             const float2 c = __ldg(Cpix + idx_col);
-                            v = mk<float>(c.x, -c.y);
+                            v[k] = mk<float>(c.x, -c.y);
                             idx_col += n - k - 1;
                         }
                     }
-                    myrow[k] = v;
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(myrow);
+#pragma unroll
+                for (int q = 0; q < NP / 2; ++q) {
+                    uint4 w;
+                    memcpy(&w, &v[2 * q], 16);
+                    dst[q] = w;
                 }
             }
             SmemRow<NP> ld{myrow};
