@@ -15,7 +15,20 @@ __global__ void __launch_bounds__(256) k_amp_stats(const float2 *__restrict__ z,
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
         float P = 0.0f, A = 0.0f;
-        for (int t = 0; t < n; ++t) {
+        int t = 0;
+        // Eight dates in flight per thread; the sums still run in date order.
+        for (; t + 8 <= n; t += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(z + (long long)(t + u) * npix + p);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float q = __fadd_rn(__fmul_rn(v[u].x, v[u].x), __fmul_rn(v[u].y, v[u].y));
+                P = __fadd_rn(P, q);
+                A = __fadd_rn(A, __fsqrt_rn(q));
+            }
+        }
+        for (; t < n; ++t) {
             const float2 v = __ldcs(z + (long long)t * npix + p);
             const float q = __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
             P = __fadd_rn(P, q);

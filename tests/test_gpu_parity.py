@@ -129,9 +129,11 @@ def test_phase_link_closed_forms(ctx):
 
 # -------------------------------------------------------------------- S7
 
-@pytest.mark.parametrize("win,first_real", [((5, 11, 3, 6), 0), ((5, 11, 1, 1), 2), ((3, 5, 4, 7), 1)])
-def test_compress_parity(ctx, win, first_real):
-    N, H, W = 6, 45, 101
+@pytest.mark.parametrize("win,first_real,N,W", [((5, 11, 3, 6), 0, 6, 101), ((5, 11, 1, 1), 2, 6, 101),
+                                                 ((3, 5, 4, 7), 1, 6, 101), ((5, 11, 3, 6), 1, 13, 600),
+                                                 ((5, 11, 1, 1), 0, 11, 530)])
+def test_compress_parity(ctx, win, first_real, N, W):
+    H = 45
     z, _ = stack(0, N=N, H=H, W=W, seed=31)
     Ho, Wo = H // win[2], W // win[3]
     rng = np.random.default_rng(1)
