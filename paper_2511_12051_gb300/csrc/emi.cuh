@@ -91,7 +91,18 @@ __device__ __forceinline__ float rcp_t(float a) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
 }
-__device__ __forceinline__ double rcp_t(double a) { return 1.0 / a; }
+// Double: the single-precision seed refined by two Newton steps
+// r <- r + r (1 - a r), each squaring the relative error (2^-23 -> 2^-46 ->
+// rounding level); outside the single-precision range, a division.
+__device__ __forceinline__ double rcp_t(double a) {
+    const double m = fabs(a);
+    if (!(m > 1e-30 && m < 1e30)) return 1.0 / a;
+    double r = (double)rcp_t((float)a);
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
 __device__ __forceinline__ float scale_s(float a, float s) { return a * s; }
 __device__ __forceinline__ double scale_s(double a, double s) { return a * s; }
 template <class T>
@@ -354,7 +365,7 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
 // Solve one pixel.  T = float: returns flag = true (and no outputs) for a pixel
 // whose single-precision result cannot be trusted to err_max, when
 // prm.fp64_resolve is set.  T = double: always produces outputs; the inversion
-// of G fails (EVD fallback) when a pivot is <= 1e-12, the limit of the FP64
+// of G fails (EVD fallback) when a pivot is <= kPivotFail, as in the FP64
 // reference.
 //
 // Shift: inverse iteration starts with mu (0.99, Sec. III-B).  When the
@@ -516,8 +527,9 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
 // shift refinement) converges first; then x <- x - B^{-1}(A x - rho x) runs in
 // double precision until the correction vanishes, so the fixed point is an
 // eigenvector of the double-precision A (preconditioned inverse iteration).
-// The inversion of G fails (EVD fallback, power iteration on C in double)
-// when a double-precision pivot is <= 1e-12.
+// The inversion of G fails (EVD fallback) when a double-precision pivot is <=
+// kPivotFail; the decision is the double-precision one, the power iteration
+// on C then runs in single precision, as do the reference phase and gamma_t.
 template <int NP, class Loader>
 __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref, const EmiParams &prm,
                                        cpx<double> *dbuf, unsigned gmask, int glane0) {
@@ -547,17 +559,26 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
     bool conv = false;
     const double tol64 = 1e-9;
     if (inv_failed) {
-        // EVD fallback: power iteration on C (in A) in double precision.
-        const cpx<double> c0 = live ? load(0) : mk<double>(0.0, 0.0);
-        const double m2 = norm2(c0);
-        x64 = (m2 > 0.0) ? (rsqrt(m2) * c0) : mk<double>(1.0, 0.0);
-        x64 = live ? (rsqrt((double)n) * x64) : mk<double>(0.0, 0.0);
-        double mu_unused = 0.0, q_unused = 0.0;
-        cpx<double> d;
-        auto noreform = [&](double) { return 1.0; };
-        conv = inverse_iteration<NP, double>(A, x64, d, mu_unused, q_unused, noreform, false, dbuf, r, live, gmask,
-                                             1e-9, prm.max_iter, false);
+        // EVD fallback, decided here in double precision: power iteration on C
+        // in single precision, as on the single-precision path (the principal
+        // eigenvector needs no more).
+        cpx<float> Cf[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) Cf[k] = mk<float>((float)A[k].x, (float)A[k].y);
+        cpx<float> xf;
+        {
+            const cpx<float> c0 = live ? Cf[0] : mk<float>(0.f, 0.f);
+            const float m2 = norm2(c0);
+            xf = (m2 > 0.f) ? (rsqrtf(m2) * c0) : mk<float>(1.f, 0.f);
+            xf = live ? (rsqrtf((float)n) * xf) : mk<float>(0.f, 0.f);
+        }
+        float mu_unused = 0.f, q_unused = 0.f;
+        cpx<float> d;
+        auto noreform = [&](float) { return 1.f; };
+        conv = inverse_iteration<NP, float>(Cf, xf, d, mu_unused, q_unused, noreform, false, fbuf, r, live, gmask,
+                                            prm.tol, prm.max_iter, false);
         lam = d.x;
+        x64 = mk<double>((double)xf.x, (double)xf.y);
     } else {
 #pragma unroll
         for (int k = 0; k < NP; ++k) A[k] = mk<double>(g[k] * A[k].x, g[k] * A[k].y);
@@ -621,19 +642,20 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
     vr.x = __shfl_sync(gmask, x64.x, glane0 + ref);
     vr.y = __shfl_sync(gmask, x64.y, glane0 + ref);
     const cpx<double> w = x64 * conj(vr);
-    float ph = atan2f((float)w.y, (float)w.x);
+    const cpx<float> wf = mk<float>((float)w.x, (float)w.y);
+    float ph = atan2f(wf.y, wf.x);
     if (r == ref || !live) ph = 0.f;
-    const double wm2 = norm2(w);
-    cpx<float> zeta = (wm2 > 0.0) ? mk<float>((float)(w.x * rsqrt(wm2)), (float)(w.y * rsqrt(wm2)))
-                                  : mk<float>(1.f, 0.f);
+    // gamma_t in single precision (as on the single-precision path).
+    const float wm2 = norm2(wf);
+    cpx<float> zeta = (wm2 > 0.f) ? (rsqrtf(wm2) * wf) : mk<float>(1.f, 0.f);
     if (r == ref) zeta = mk<float>(1.f, 0.f);
     cpx<float> u[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        const cpx<double> ck = (live && k < n) ? load(k) : mk<double>(0.0, 0.0);
-        const double m2 = norm2(ck);
-        const cpx<float> uk = (m2 > 0.0) ? mk<float>((float)(ck.x * rsqrt(m2)), (float)(ck.y * rsqrt(m2)))
-                                         : mk<float>(1.f, 0.f);
+        const cpx<double> cd = (live && k < n) ? load(k) : mk<double>(0.0, 0.0);
+        const cpx<float> ck = mk<float>((float)cd.x, (float)cd.y);
+        const float m2 = norm2(ck);
+        const cpx<float> uk = (m2 > 0.f) ? (rsqrtf(m2) * ck) : mk<float>(1.f, 0.f);
         u[k] = (k > r && k < n) ? uk : mk<float>(0.f, 0.f);
     }
     const cpx<float> rowsum = group_matvec<NP, float>(u, zeta, fbuf, r, gmask);

@@ -41,7 +41,9 @@ constexpr int kEmiWarps = 4;
 // Work counter of the double-precision re-solve (one per context): warps take
 // 32-pixel chunks of the status array in turn, so the few long-running pending
 // pixels spread over all resident warps instead of waiting for the chunks
-// statically assigned to them.  Reset by k_reset_counter before each re-solve
+// statically assigned to them.  Chunk c holds pixels c, c + nchunks, ...,
+// c + 31 nchunks: pending pixels cluster in space, and interleaving spreads a
+// cluster over many chunks (and warps).  Reset by k_reset_counter before each re-solve
 // launch (stream order).
 __global__ void k_reset_counter(unsigned long long *c) { *c = 0; }
 
@@ -151,10 +153,11 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restri
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
+    const long long nchunks = (npx + 31) / 32;
     for (;;) {
-        const long long base = next_chunk(prm.work, lane) * 32;
-        if (base >= npx) break;
-        const long long pl = base + lane;
+        const long long base = next_chunk(prm.work, lane);
+        if (base >= nchunks) break;
+        const long long pl = base + (long long)lane * nchunks;  // interleaved: clusters spread over chunks
         const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
         unsigned bal = __ballot_sync(0xffffffffu, pend);
         while (bal) {
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restri
                 }
             }
             if (mine >= 0) {
-                const long long p = base + mine;
+                const long long p = base + (long long)mine * nchunks;
                 PackedRow<double> ld{C + p * nt, n, r};
                 const PixelResult res = emi_solve_mixed<NP>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0);
                 if (r < n) phase[(long long)r * npx + p] = res.phase;
@@ -209,10 +212,11 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
     const int grp = lane / NP, r = lane - grp * NP;
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const long long nchunks = (npx + 31) / 32;
     for (;;) {
-        const long long base = next_chunk(prm.work, lane) * 32;
-        if (base >= npx) break;
-        const long long pl = base + lane;
+        const long long base = next_chunk(prm.work, lane);
+        if (base >= nchunks) break;
+        const long long pl = base + (long long)lane * nchunks;  // interleaved: clusters spread over chunks
         const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
         unsigned bal = __ballot_sync(0xffffffffu, pend);
         while (bal) {
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
                 }
             }
             if (mine >= 0) {
-                const long long p = base + mine;
+                const long long p = base + (long long)mine * nchunks;
                 const int oy = (int)(p / g.Wo), ox = (int)(p - (p / g.Wo) * g.Wo);
                 const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
                 const uint64_t *mw = mask + p * g.nwords;
@@ -253,31 +257,27 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
                             }
                         }
                     }
-                // normalise: C_rk = S_rk / sqrt(S_rr S_kk), C_rr = 1
+                // normalise: C_rk = S_rk s_r s_k with s_i = 1/sqrt(S_ii) (0 when
+                // S_ii = 0), C_rr = 1; one square root per lane.
                 cpx<double> *buf = &sbuf[warp][glane0];
                 double d_own = 0.0;
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
                     if (k == r) d_own = row.c[k].x;
-                buf[r] = mk<double>(d_own, 0.0);
+                const double s_own = (d_own > 0.0) ? 1.0 / sqrt(d_own) : 0.0;
+                buf[r] = mk<double>(s_own, 0.0);
                 __syncwarp(gmask);
                 const uint4 *src = reinterpret_cast<const uint4 *>(buf);
 #pragma unroll
                 for (int q4 = 0; q4 < NP / E; ++q4) {
                     const uint4 v = src[q4];
-                    cpx<double> dk[E];
-                    memcpy(dk, &v, 16);
+                    cpx<double> sk[E];
+                    memcpy(sk, &v, 16);
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const int k = q4 * E + e;
-                        const double prod = d_own * dk[e].x;
-                        cpx<double> cv;
-                        if (k == r) cv = mk<double>(1.0, 0.0);
-                        else if (d_own > 0.0 && dk[e].x > 0.0) {
-                            const double s = 1.0 / sqrt(prod);
-                            cv = mk<double>(row.c[k].x * s, row.c[k].y * s);
-                        } else cv = mk<double>(0.0, 0.0);
-                        row.c[k] = cv;
+                        const double sc = s_own * sk[e].x;
+                        row.c[k] = (k == r) ? mk<double>(1.0, 0.0) : mk<double>(row.c[k].x * sc, row.c[k].y * sc);
                     }
                 }
                 __syncwarp(gmask);
