@@ -50,12 +50,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 # DRAM bytes per output pixel of a launch, from the ncu capture summarised in
-# profiles/k_emi32_k_cov_tma_1024x4096.md (1024x4096 case; traffic grows with
+# profiles/k_emi32_k_cov_async_1024x4096.md (1024x4096 case; traffic grows with
 # the pixel count).  Valid for the kernel versions profiled there: a kernel
 # changed since its capture must drop out of this table (traffic null).
 NCU_DRAM_BYTES_PER_OUTPUT_PX = {
-    "phase_link_fp32": (223.641088e6 + 17.391616e6) / 232562,
-    "covariance": (510.597632e6 + 196.865536e6) / 232562,
+    "phase_link_fp32": (223.649280e6 + 13.100032e6) / 232562,
+    "covariance": (516.021504e6 + 204.250880e6) / 232562,
 }
 
 
