@@ -197,6 +197,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--rows", type=int, default=H_FULL, help="image rows (smaller cases for profiling only)")
     ap.add_argument("--cols", type=int, default=W_FULL, help="image columns (smaller cases for profiling only)")
+    ap.add_argument("--cov-precision", default="fp32", choices=["fp32", "bf16"],
+                    help="coherence arithmetic of the timed step (fp32: the plain path)")
+    ap.add_argument("--no-modes", action="store_true", help="skip timing the bfloat16-coherence mode beside it")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -224,7 +227,8 @@ def main():
     stream = torch.cuda.Stream(dev)
     ctx = plk.Context(dev, stream)
     st = plk.State(ctx, spec.H, spec.W, WINDOW, K_max=6, M_max=N_DATES)
-    params = plk.default_params()
+    prec = plk.COV_BF16 if args.cov_precision == "bf16" else plk.COV_FP32
+    params = plk.default_params(cov_precision=prec)
     with torch.cuda.stream(stream):
         out = st.step(z, params)  # allocates the output tensors once
     torch.cuda.synchronize(dev)
@@ -324,6 +328,37 @@ def main():
                "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_e2e / ne}
         del zh, oh
 
+    # ------------------------------------- bfloat16-coherence mode beside it
+    modes = None
+    if not args.no_modes and prec == plk.COV_FP32:
+        alt = plk.default_params(cov_precision=plk.COV_BF16)
+
+        def alt_step():
+            st.reset()
+            st.step(z, alt, out=out)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                alt_step()
+        torch.cuda.synchronize(dev)
+        ctx.profile(True)
+        pdist.barrier()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            g0.record(stream)
+            for _ in range(args.steps):
+                alt_step()
+            g1.record(stream)
+        torch.cuda.synchronize(dev)
+        kalt = ctx.profile_collect()
+        ctx.profile(False)
+        ms_alt = pdist.max_over_ranks(g0.elapsed_time(g1), dev)
+        modes = {"bf16_covariance": {
+            "value": npx * world * args.steps / (ms_alt / 1e3), "unit": UNIT, "ms_per_step": ms_alt / args.steps,
+            "kernels_ms_per_step": {kk: v[0] / args.steps for kk, v in kalt.items()},
+            "accuracy": "measured against the FP64 oracle by tests/test_gpu_bf16.py (linked-phase p50/p99/max)"}}
+
     # ---------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -352,6 +387,8 @@ def main():
             "clocks": clk,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kernels.items()},
             "pixel_status_hist": status_hist,
+            "cov_precision": args.cov_precision,
+            "modes": modes,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -73,7 +73,7 @@ typedef struct plk_params {
     int32_t max_iter;  /* inverse-iteration cap, all shifts together; default 100 */
     float cond_max;    /* pixels whose 1-norm condition number of G exceeds
                           cond_max, or whose single-precision inversion of G meets
-                          a pivot below 1e-6 without C being rank one, are
+                          a pivot within 2e-5 of the 1e-4 failure limit, are
                           re-solved in double precision; default 1e4 */
     int32_t fp64_resolve; /* 1 (default): re-solve flagged pixels in FP64; 0: keep
                              the single-precision result */
@@ -82,8 +82,15 @@ typedef struct plk_params {
                           eigengap seen by the iteration) exceeds err_max are
                           re-solved in double precision; default 0.1 (the bound
                           is loose: measured errors sit 1e3-1e4 below it) */
-    int32_t reserved[3];
+    int32_t cov_precision; /* coherence arithmetic (S3): PLK_COV_FP32 (default) or
+                              PLK_COV_BF16 (samples rounded to bfloat16, sums in
+                              single precision on the tensor cores; N <= 32) */
+    int32_t reserved[2];
 } plk_params;
+
+/* Coherence precision modes (plk_params.cov_precision, plk_estimate_covariance). */
+#define PLK_COV_FP32 0
+#define PLK_COV_BF16 1
 
 typedef struct plk_ctx plk_ctx;
 typedef struct plk_state plk_state;
@@ -163,9 +170,13 @@ plk_status plk_shp_select(plk_ctx *ctx, const float *sum_pow, int n_eff, int H, 
  * C_ik = 0 where S_ii or S_kk is 0; an empty mask gives NaN entries.
  * slc [N][H][W]; mask as written by plk_shp_select for the same window;
  * C_packed [Ho][Wo][N(N+1)/2], upper triangle by rows: entry (i, k), i <= k,
- * at i*N - i*(i-1)/2 + (k - i).  Single-precision accumulation. */
+ * at i*N - i*(i-1)/2 + (k - i).  precision PLK_COV_FP32: single-precision
+ * products and sums; PLK_COV_BF16: the samples are rounded to bfloat16 (round
+ * to nearest even) and the products summed in single precision on the tensor
+ * cores, N <= 32 (EUNSUPPORTED beyond). */
 plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W,
-                                   plk_window win, const uint64_t *mask, plk_c64 *C_packed);
+                                   plk_window win, const uint64_t *mask, int precision,
+                                   plk_c64 *C_packed);
 
 /* S4-S6. EMI phase linking (Sec. III-B, eq. (emi-eigenvalue-problem)) with the
  * reference of Sec. II-A and gamma_t of Sec. III-C, eq. (temporal-coherence).

@@ -330,10 +330,13 @@ plk_status plk_shp_select(plk_ctx *ctx, const float *sum_pow, int n_eff, int H, 
 }
 
 plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W, plk_window win,
-                                   const uint64_t *mask, plk_c64 *C_packed) {
+                                   const uint64_t *mask, int precision, plk_c64 *C_packed) {
     if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_estimate_covariance: null ctx");
-    if (!slc || N < 2 || N > PLK_MAX_N || H < 1 || W < 1 || !window_ok(win))
+    if (!slc || N < 2 || N > PLK_MAX_N || H < 1 || W < 1 || !window_ok(win) ||
+        (precision != PLK_COV_FP32 && precision != PLK_COV_BF16))
         return fail(ctx, PLK_EINVAL, "plk_estimate_covariance: bad argument");
+    if (precision == PLK_COV_BF16 && N > 32)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_estimate_covariance: bfloat16 mode needs N <= 32 (N=%d)", N);
     if ((long long)(H / win.sy) * (W / win.sx) > 0 && (!mask || !C_packed))
         return fail(ctx, PLK_EINVAL, "plk_estimate_covariance: null pointer");
     if (!aligned(slc, 8) || !aligned(mask, 8) || !aligned(C_packed, 8))
@@ -343,7 +346,8 @@ plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int 
     Planes z{};
     for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
     ctx->prof.begin("covariance", ctx->stream);
-    cudaError_t e = plk::launch_covariance(z, N, g, mask, reinterpret_cast<float2 *>(C_packed), ctx->stream);
+    cudaError_t e =
+        plk::launch_covariance(z, N, g, mask, reinterpret_cast<float2 *>(C_packed), ctx->stream, precision);
     ctx->prof.end(ctx->stream);
     if (e == cudaErrorInvalidConfiguration)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_estimate_covariance: window %dx%d with N=%d exceeds shared memory",
@@ -352,14 +356,17 @@ plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int 
     return PLK_OK;
 }
 
-static plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha) {
+static plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
+                                 int *cov_precision = nullptr) {
     out->work = ctx->work;
     plk_params p;
     if (params) p = *params;
     else plk_default_params(&p);
     if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
-        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0))
+        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0) ||
+        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16))
         return fail(ctx, PLK_EINVAL, "bad plk_params");
+    if (cov_precision) *cov_precision = p.cov_precision;
     out->beta = p.beta;
     out->mu = p.mu;
     out->tol = p.tol;
@@ -598,8 +605,11 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     if (st->device != ctx->device) return fail(ctx, PLK_EINVAL, "plk_ministack_step: state on another device");
     plk::EmiParams prm;
     double alpha;
-    plk_status ps = resolve_params(ctx, params, &prm, &alpha);
+    int cov_precision = PLK_COV_FP32;
+    plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision);
     if (ps != PLK_OK) return ps;
+    if (cov_precision == PLK_COV_BF16 && st->K_used + M > 32)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: bfloat16 coherence needs N <= 32");
     DeviceGuard dg(ctx->device);
     const Geom g = plk::make_geom(st->H, st->W, st->win);
     const long long npix = (long long)st->H * st->W, nout = (long long)g.Ho * g.Wo;
@@ -632,7 +642,7 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
 
     // S3-S6.
     ctx->prof.begin("covariance", s);
-    e = plk::launch_covariance(z, N, g, st->mask, st->C, s);
+    e = plk::launch_covariance(z, N, g, st->mask, st->C, s, cov_precision);
     ctx->prof.end(s);
     if (e == cudaErrorInvalidConfiguration)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: window with N=%d exceeds shared memory", N);

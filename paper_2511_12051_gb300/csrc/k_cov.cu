@@ -28,13 +28,11 @@
 // up sets a device flag (read by plk_sync) and the CTA returns.
 // k_cov_plain loads with ordinary coalesced loads (no alignment needs); it is
 // used when a plane is not 16-byte aligned, W is odd or a box is too large.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 
 #include "cpx.cuh"
 #include "plk_internal.cuh"
+#include "tma.cuh"
 
 namespace plk {
 
@@ -225,44 +223,6 @@ __global__ void __launch_bounds__(256) k_cov_plain(const __grid_constant__ Plane
 }
 
 // --------------------------------------------------------------- TMA path
-
-struct TmaMaps {
-    CUtensorMap m[PLK_MAX_N];
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait (about a second): false if the phase never completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
-    for (int i = 0; i < (1 << 22); ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i > 32) __nanosleep(256);
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
 
 template <int B, int BN>
 __global__ void __launch_bounds__(256, 1) k_cov_tma(const __grid_constant__ TmaMaps tm, int n, const Geom g,
@@ -556,22 +516,6 @@ static CovLayout choose_layout(int n, int B, int BN, int S, const Geom &g, size_
     return best;
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-        cudaGetLastError();
-    }
-    return fn;
-}
-
 template <int B, int BN>
 static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                            cudaStream_t s) {
@@ -601,37 +545,18 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
         }
     }
 #endif
-    bool tma = (g.W % 2 == 0) && tensor_map_encoder() != nullptr;
-    for (int d = 0; d < n && tma; ++d) tma = ((uintptr_t)z.p[d] % 16) == 0;
-    CovLayout lay{};
-    if (tma) {
-        lay = choose_layout(n, B, BN, S, g, kMaxSmem, true);
-        tma = lay.TY > 0;
-    }
-    if (tma) {
-        TmaMaps maps;
-        const cuuint64_t dims[2] = {(cuuint64_t)g.W, (cuuint64_t)g.H};
-        const cuuint64_t strides[1] = {(cuuint64_t)g.W * sizeof(float2)};
-        const cuuint32_t box[2] = {(cuuint32_t)lay.RX, (cuuint32_t)lay.RY};
-        const cuuint32_t estr[2] = {1, 1};
-        for (int d = 0; d < n && tma; ++d) {
-            CUresult r = tensor_map_encoder()(&maps.m[d], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
-                                              const_cast<float2 *>(z.p[d]), dims, strides, box, estr,
-                                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            tma = (r == CUDA_SUCCESS);
-        }
-        if (tma) {
-            cudaError_t e = cudaFuncSetAttribute(k_cov_tma<B, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)kMaxSmem);
-            if (e != cudaSuccess) return e;
-            const int tilesY = (g.Ho + lay.TY - 1) / lay.TY;
-            const long long ntiles = (long long)tilesY * ((g.Wo + lay.TX - 1) / lay.TX);
-            if (ntiles == 0) return cudaSuccess;
-            const long long grid = std::min<long long>(ntiles, device_sm_count());
-            k_cov_tma<B, BN><<<(unsigned)grid, 256, lay.smem_tma, s>>>(maps, n, g, mask, C, lay, ntiles, tilesY);
-            return cudaGetLastError();
-        }
+    CovLayout lay = choose_layout(n, B, BN, S, g, kMaxSmem, true);
+    TmaMaps maps;
+    if (lay.TY > 0 && encode_plane_maps(maps, z, n, g, lay.RX, lay.RY)) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_cov_tma<B, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (e != cudaSuccess) return e;
+        const int tilesY = (g.Ho + lay.TY - 1) / lay.TY;
+        const long long ntiles = (long long)tilesY * ((g.Wo + lay.TX - 1) / lay.TX);
+        if (ntiles == 0) return cudaSuccess;
+        const long long grid = std::min<long long>(ntiles, device_sm_count());
+        k_cov_tma<B, BN><<<(unsigned)grid, 256, lay.smem_tma, s>>>(maps, n, g, mask, C, lay, ntiles, tilesY);
+        return cudaGetLastError();
     }
     lay = choose_layout(n, B, BN, S, g, 96 * 1024, false);
     if (lay.TY == 0) lay = choose_layout(n, B, BN, S, g, kMaxSmem, false);
@@ -649,7 +574,8 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
 }
 
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
-                              cudaStream_t s) {
+                              cudaStream_t s, int precision) {
+    if (precision == 1) return launch_covariance_bf16(z, n, g, mask, C, s);
     // 3 x 3 block grid (5 pixels per warp) up to N = 18; 5 x 5 (2 per warp) beyond
     // (blocks of 5 or more dates: 4-date blocks on a 5 x 5 grid collide in banks).
     if (n <= 3) return run_cov<1, 3>(z, n, g, mask, C, s);

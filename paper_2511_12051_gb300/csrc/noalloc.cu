@@ -63,8 +63,11 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
     if (params) p = *params;
     else plk_default_params(&p);
     if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.tol > 0) || p.max_iter < 1 ||
-        !(p.cond_max > 0) || !(p.err_max > 0))
+        !(p.cond_max > 0) || !(p.err_max > 0) ||
+        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16))
         return fail(PLK_EINVAL, "plk_phase_link_stack_noalloc: bad plk_params");
+    if (p.cov_precision == PLK_COV_BF16 && N > 32)
+        return fail(PLK_EUNSUPPORTED, "plk_phase_link_stack_noalloc: bfloat16 coherence needs N <= 32");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -107,7 +110,7 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
     if (e != cudaSuccess) return fail(PLK_ECUDA, "plk_phase_link_stack_noalloc: shp launch failed");
     plk::Planes z{};
     for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * npix;
-    e = plk::launch_covariance(z, N, g, mask, C, s);
+    e = plk::launch_covariance(z, N, g, mask, C, s, p.cov_precision);
     if (e == cudaErrorInvalidConfiguration)
         return fail(PLK_EUNSUPPORTED, "plk_phase_link_stack_noalloc: window too large for shared memory");
     if (e != cudaSuccess) return fail(PLK_ECUDA, "plk_phase_link_stack_noalloc: covariance launch failed");

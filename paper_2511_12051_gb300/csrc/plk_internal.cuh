@@ -54,7 +54,10 @@ cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *m
 // Returns cudaErrorInvalidConfiguration if the window/N combination exceeds
 // shared memory even at a 1x1 output tile.
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
-                              cudaStream_t s);
+                              cudaStream_t s, int precision = 0);
+// precision 1: bfloat16 samples, tensor-core sums (n <= 32).
+cudaError_t launch_covariance_bf16(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
+                                   cudaStream_t s);
 struct Prof;
 // Where the double-precision re-solve recomputes a pixel's coherence from:
 // the stack planes, geometry and SHP masks of the mini-stack.

@@ -40,7 +40,12 @@ class Window(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_float), ("mu", ctypes.c_float),
                 ("tol", ctypes.c_float), ("max_iter", ctypes.c_int32), ("cond_max", ctypes.c_float),
-                ("fp64_resolve", ctypes.c_int32), ("err_max", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+                ("fp64_resolve", ctypes.c_int32), ("err_max", ctypes.c_float), ("cov_precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+COV_FP32 = 0  # PLK_COV_FP32
+COV_BF16 = 1  # PLK_COV_BF16
 
 
 _lock = threading.Lock()
@@ -59,7 +64,7 @@ _SIGS = {
     "plk_glrt_threshold": [ctypes.c_double, _I, ctypes.POINTER(ctypes.c_double)],
     "plk_amp_stats": [_P, _P, _I, _I, _I, _P, _P, _I],
     "plk_shp_select": [_P, _P, _I, _I, _I, Window, ctypes.c_double, _P, _P],
-    "plk_estimate_covariance": [_P, _P, _I, _I, _I, Window, _P, _P],
+    "plk_estimate_covariance": [_P, _P, _I, _I, _I, Window, _P, _I, _P],
     "plk_phase_link": [_P, _P, _I, ctypes.c_int64, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_compress": [_P, _P, _I, _I, _I, _I, Window, _P, _P],
     "plk_state_create": [_P, _I, _I, Window, _I, _I, ctypes.POINTER(_P)],
@@ -231,7 +236,8 @@ class Context:
                                     _ptr(count)), self.h)
         return mask, count
 
-    def estimate_covariance(self, slc: torch.Tensor, win, mask: torch.Tensor, C: torch.Tensor | None = None):
+    def estimate_covariance(self, slc: torch.Tensor, win, mask: torch.Tensor, C: torch.Tensor | None = None,
+                            precision: int = COV_FP32):
         _need(slc, torch.complex64, "slc", self.device)
         _need(mask, torch.int64, "mask", self.device)
         N, H, W = slc.shape
@@ -240,7 +246,8 @@ class Context:
         if C is None:
             C = torch.empty((Ho, Wo, N * (N + 1) // 2), dtype=torch.complex64, device=self.device)
         _need(C, torch.complex64, "C", self.device)
-        _check(lib().plk_estimate_covariance(self.h, _ptr(slc), N, H, W, w, _ptr(mask), _ptr(C)), self.h)
+        _check(lib().plk_estimate_covariance(self.h, _ptr(slc), N, H, W, w, _ptr(mask), int(precision), _ptr(C)),
+               self.h)
         return C
 
     def phase_link(self, C: torch.Tensor, N: int, ref: int, params: Params | None = None,
