@@ -13,7 +13,7 @@
 
 namespace {
 
-__device__ __align__(256) unsigned char g_noalloc_scratch[PLK_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PLK_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
