@@ -241,6 +241,51 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
                               const plk_params *params, float *phase, float *tcoh,
                               uint8_t *status, uint16_t *shp_count);
 
+/* ------------------------------------------------ batches of stacks */
+
+/* One independent stack of a batch: its SLCs and where its outputs go (all
+ * device pointers, owned by the caller, fixed for the batch's life). */
+typedef struct plk_stack_desc {
+    const plk_c64 *slc;  /* [N][H][W] */
+    int32_t N, H, W;     /* 2 <= N <= PLK_MAX_N; H, W >= 1 */
+    int32_t ref_idx;     /* reference date of the linked phases, 0 <= ref_idx < N */
+    float *phase;        /* [N][Ho][Wo] */
+    float *tcoh;         /* [Ho][Wo] or NULL */
+    uint8_t *status;     /* [Ho][Wo] */
+} plk_stack_desc;
+
+typedef struct plk_batch plk_batch;
+
+/* A batch runs S1-S6 (Sec. III-A, II-A, III-B, III-C) for many independent
+ * stacks of uneven length N with one window: for each stack, amplitude sums
+ * over its N dates, GLRT SHP selection with n_eff = N, coherence, EMI with its
+ * ref_idx, gamma_t -- the same results as plk_phase_link_stack_noalloc (and as
+ * plk_ministack_step on a fresh state for ref_idx = 0).  The paper processes
+ * bursts one after another; this serves many bursts, or many small
+ * mini-stacks, in one call.  plk_batch_create checks the descriptors, copies
+ * them and allocates every stack's scratch (sums, masks, counts, coherence, a
+ * re-solve counter); the caller's arrays must stay valid until
+ * plk_batch_destroy.  Errors: EINVAL (bad descriptor or window, with the
+ * stack index), EUNSUPPORTED (bfloat16 coherence with N > 32), ENOMEM, ECUDA. */
+plk_status plk_batch_create(plk_ctx *ctx, const plk_stack_desc *stacks, int n_stacks, plk_window win,
+                            const plk_params *params, plk_batch **out);
+/* Run every stack.  The first call tunes the launch schedule for each
+ * distinct (N, window) not yet tuned in ctx (it times candidate coherence
+ * tiles and EMI lanes per pixel on the batch's own data, so that call runs
+ * the stages several times and waits for them), then records the whole batch
+ * -- stacks spread over several streams, longest first -- as one CUDA graph;
+ * every call (the first included) then launches that graph on ctx's stream.
+ * Errors: ECUDA (with the failing stage), EINVAL. */
+plk_status plk_batch_run(plk_ctx *ctx, plk_batch *b);
+/* graph_built: 1 once recorded; streams: branches of the graph; nodes: graph
+ * nodes (kernels and dependencies). */
+plk_status plk_batch_info(const plk_batch *b, int *graph_built, int *streams, int *nodes);
+plk_status plk_batch_destroy(plk_batch *b);
+/* The schedule the autotuner chose for (N, window) in ctx: coherence tile
+ * (output pixels) and EMI lanes per pixel; EINVAL if not tuned. */
+plk_status plk_tuned_schedule(const plk_ctx *ctx, int N, plk_window win, int *cov_tile_y, int *cov_tile_x,
+                              int *emi_lanes);
+
 /* ------------------------------------------- allocation-free variant */
 
 /* Scratch capacity of plk_phase_link_stack_noalloc, in bytes: one array of

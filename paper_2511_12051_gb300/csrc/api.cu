@@ -8,20 +8,7 @@
 
 #include <new>
 
-#include "plk_internal.cuh"
-
-struct plk_ctx {
-    int device;
-    cudaStream_t stream;
-    unsigned long long *work;  // device counter of the FP64 re-solve
-    char err[512];
-    plk::Prof prof;
-    // aggregated by plk_profile_collect
-    int n_agg;
-    const char *agg_name[32];
-    double agg_ms[32];
-    int agg_count[32];
-};
+#include "api_internal.h"
 
 struct plk_state {
     int device;
@@ -39,8 +26,10 @@ struct plk_state {
 };
 
 namespace {
-
 thread_local char g_noctx_err[512];
+}  // namespace
+
+namespace plkapi {
 
 plk_status fail(plk_ctx *ctx, plk_status st, const char *fmt, ...) {
     char *dst = ctx ? ctx->err : g_noctx_err;
@@ -55,25 +44,16 @@ plk_status cuda_fail(plk_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, PLK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Make ctx's device current for the duration of a call.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 bool window_ok(plk_window w) {
     return w.wy >= 1 && w.wx >= 1 && (w.wy & 1) && (w.wx & 1) && w.sy >= 1 && w.sx >= 1 &&
            (long long)w.wy * w.wx <= PLK_MAX_WINDOW;
 }
 
-bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+}  // namespace plkapi
+
+using namespace plkapi;
+
+namespace {
 
 // Regularised incomplete beta I_x(a, b) by the continued fraction for the
 // incomplete beta function (evaluated with the modified Lentz method), with
@@ -130,6 +110,28 @@ int device_sm_count() {
 using plk::Geom;
 using plk::Planes;
 
+plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
+                                  int *cov_precision) {
+    out->work = ctx->work;
+    plk_params p;
+    if (params) p = *params;
+    else plk_default_params(&p);
+    if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
+        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0) ||
+        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16))
+        return fail(ctx, PLK_EINVAL, "bad plk_params");
+    if (cov_precision) *cov_precision = p.cov_precision;
+    out->beta = p.beta;
+    out->mu = p.mu;
+    out->tol = p.tol;
+    out->cond_max = p.cond_max;
+    out->err_max = p.err_max;
+    out->max_iter = p.max_iter;
+    out->fp64_resolve = p.fp64_resolve ? 1 : 0;
+    if (alpha) *alpha = p.alpha;
+    return PLK_OK;
+}
+
 extern "C" {
 
 plk_status plk_default_params(plk_params *p) {
@@ -185,6 +187,7 @@ plk_status plk_create(plk_ctx **out, int device, void *cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->err[0] = 0;
     ctx->n_agg = 0;
+    ctx->n_tuned = 0;
     ctx->work = nullptr;
     {
         DeviceGuard dg(device);
@@ -356,27 +359,6 @@ plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int 
     return PLK_OK;
 }
 
-static plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
-                                 int *cov_precision = nullptr) {
-    out->work = ctx->work;
-    plk_params p;
-    if (params) p = *params;
-    else plk_default_params(&p);
-    if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
-        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0) ||
-        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16))
-        return fail(ctx, PLK_EINVAL, "bad plk_params");
-    if (cov_precision) *cov_precision = p.cov_precision;
-    out->beta = p.beta;
-    out->mu = p.mu;
-    out->tol = p.tol;
-    out->cond_max = p.cond_max;
-    out->err_max = p.err_max;
-    out->max_iter = p.max_iter;
-    out->fp64_resolve = p.fp64_resolve ? 1 : 0;
-    if (alpha) *alpha = p.alpha;
-    return PLK_OK;
-}
 
 plk_status plk_phase_link(plk_ctx *ctx, const plk_c64 *C_packed, int N, int64_t npx, int ref_idx,
                           const plk_params *params, float *phase, float *tcoh, float *lambda_min,

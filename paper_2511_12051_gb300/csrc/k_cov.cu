@@ -516,9 +516,50 @@ static CovLayout choose_layout(int n, int B, int BN, int S, const Geom &g, size_
     return best;
 }
 
+// Block shape for n dates, as launch_covariance dispatches: B x B register
+// blocks on a BN x BN grid.
+static void block_shape(int n, int &B, int &BN) {
+    BN = n <= 18 ? 3 : 5;
+    B = (n + BN - 1) / BN;
+    if (BN == 5 && B < 5) B = 5;  // 4-date blocks on a 5 x 5 grid collide in banks
+}
+
+int covariance_tile_candidates(int n, const Geom &g, int (*tiles)[2], int max) {
+    int B, BN;
+    block_shape(n, B, BN);
+    const int S = (B * BN) % 2 ? B * BN : B * BN + 1;
+    const int ppw = 32 / (BN * (BN + 1) / 2);
+    const size_t kHalfSm = 113 * 1024;
+    struct Cand {
+        double score;
+        int TY, TX;
+    };
+    Cand c[256];
+    int nc = 0;
+    for (int a = 1; a <= 4; ++a)
+        for (int TX = 1; TX <= 64 && nc < 256; ++TX) {
+            const int TY = ppw * a;
+            const int px = TY * TX;
+            if (px > 8 * ppw * 8) continue;
+            CovLayout l = make_layout(n, B, BN, S, g, TY, TX);
+            if (l.smem_plain > kHalfSm) continue;
+            const double halo = (double)(TY * g.sy) * (TX * g.sx) / ((double)l.RY * l.RX);
+            const int per_pass = 8 * ppw;
+            const double lane_eff = (double)px / (((px + per_pass - 1) / per_pass) * per_pass);
+            c[nc++] = {lane_eff * (0.6 + 0.4 * halo), TY, TX};
+        }
+    std::sort(c, c + nc, [](const Cand &x, const Cand &y) { return x.score > y.score; });
+    const int m = std::min(nc, max);
+    for (int i = 0; i < m; ++i) {
+        tiles[i][0] = c[i].TY;
+        tiles[i][1] = c[i].TX;
+    }
+    return m;
+}
+
 template <int B, int BN>
 static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
-                           cudaStream_t s) {
+                           cudaStream_t s, const Schedule *sch) {
     constexpr int S = PixStride<B, BN>::value;
     const size_t kMaxSmem = 226 * 1024;
 #ifndef PLK_COV_NO_ASYNC
@@ -526,7 +567,12 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
         // Two CTAs per SM: each compute buffer within half the SM's shared
         // memory (less the per-CTA reservation).
         const size_t kHalfSm = 113 * 1024;
-        CovLayout la = choose_layout(n, B, BN, S, g, kHalfSm, false);
+        CovLayout la{};
+        if (sch && sch->cov_TY > 0 && sch->cov_TX > 0 && sch->cov_TY % (32 / (BN * (BN + 1) / 2)) == 0) {
+            la = make_layout(n, B, BN, S, g, sch->cov_TY, sch->cov_TX);
+            if (la.smem_plain > kHalfSm) la = CovLayout{};
+        }
+        if (la.TY == 0) la = choose_layout(n, B, BN, S, g, kHalfSm, false);
         if (la.TY > 0) {
             cudaError_t e = cudaFuncSetAttribute(k_cov_async<B, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kHalfSm);
@@ -574,19 +620,20 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
 }
 
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
-                              cudaStream_t s, int precision) {
+                              cudaStream_t s, int precision, const Schedule *sch) {
     if (precision == 1) return launch_covariance_bf16(z, n, g, mask, C, s);
     // 3 x 3 block grid (5 pixels per warp) up to N = 18; 5 x 5 (2 per warp) beyond
     // (blocks of 5 or more dates: 4-date blocks on a 5 x 5 grid collide in banks).
-    if (n <= 3) return run_cov<1, 3>(z, n, g, mask, C, s);
-    if (n <= 6) return run_cov<2, 3>(z, n, g, mask, C, s);
-    if (n <= 9) return run_cov<3, 3>(z, n, g, mask, C, s);
-    if (n <= 12) return run_cov<4, 3>(z, n, g, mask, C, s);
-    if (n <= 15) return run_cov<5, 3>(z, n, g, mask, C, s);
-    if (n <= 18) return run_cov<6, 3>(z, n, g, mask, C, s);
-    if (n <= 25) return run_cov<5, 5>(z, n, g, mask, C, s);
-    if (n <= 30) return run_cov<6, 5>(z, n, g, mask, C, s);
-    return run_cov<7, 5>(z, n, g, mask, C, s);
+    // Kept in step with block_shape().
+    if (n <= 3) return run_cov<1, 3>(z, n, g, mask, C, s, sch);
+    if (n <= 6) return run_cov<2, 3>(z, n, g, mask, C, s, sch);
+    if (n <= 9) return run_cov<3, 3>(z, n, g, mask, C, s, sch);
+    if (n <= 12) return run_cov<4, 3>(z, n, g, mask, C, s, sch);
+    if (n <= 15) return run_cov<5, 3>(z, n, g, mask, C, s, sch);
+    if (n <= 18) return run_cov<6, 3>(z, n, g, mask, C, s, sch);
+    if (n <= 25) return run_cov<5, 5>(z, n, g, mask, C, s, sch);
+    if (n <= 30) return run_cov<6, 5>(z, n, g, mask, C, s, sch);
+    return run_cov<7, 5>(z, n, g, mask, C, s, sch);
 }
 
 }  // namespace plk

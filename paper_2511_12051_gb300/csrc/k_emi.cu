@@ -324,10 +324,14 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
 
 cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
                               float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s, Prof *prof,
-                              const StackSource *src) {
+                              const StackSource *src, const Schedule *sch) {
     if (npx == 0) return cudaSuccess;
-    if (n <= 8) return run_emi<8>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
-    if (n <= 16) return run_emi<16>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+    // Lanes per pixel: the smallest group that holds a row, unless the
+    // schedule asks for a wider one (fewer pixels per warp).
+    int np = n <= 8 ? 8 : (n <= 16 ? 16 : 32);
+    if (sch && sch->emi_np >= np && (sch->emi_np == 16 || sch->emi_np == 32)) np = sch->emi_np;
+    if (np == 8) return run_emi<8>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+    if (np == 16) return run_emi<16>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
     return run_emi<32>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
 }
 

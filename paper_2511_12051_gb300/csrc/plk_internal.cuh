@@ -53,8 +53,17 @@ cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *m
                        cudaStream_t s);
 // Returns cudaErrorInvalidConfiguration if the window/N combination exceeds
 // shared memory even at a 1x1 output tile.
+// Launch schedule chosen by the batch autotuner (0 = the built-in heuristic).
+struct Schedule {
+    int cov_TY = 0, cov_TX = 0;  // single-precision coherence tile (output pixels)
+    int emi_np = 0;              // lanes per pixel in the EMI kernels (8, 16 or 32, >= n)
+};
+
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
-                              cudaStream_t s, int precision = 0);
+                              cudaStream_t s, int precision = 0, const Schedule *sch = nullptr);
+// Up to max candidate single-precision coherence tiles {TY, TX} for (n, g),
+// best heuristic score first; returns the count.
+int covariance_tile_candidates(int n, const Geom &g, int (*tiles)[2], int max);
 // precision 1: bfloat16 samples, tensor-core sums (n <= 32).
 cudaError_t launch_covariance_bf16(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                                    cudaStream_t s);
@@ -68,7 +77,7 @@ struct StackSource {
 };
 cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
                               float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s,
-                              Prof *prof = nullptr, const StackSource *src = nullptr);
+                              Prof *prof = nullptr, const StackSource *src = nullptr, const Schedule *sch = nullptr);
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
                             float2 *kappa, cudaStream_t s);
 

@@ -44,6 +44,12 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2)]
 
 
+class StackDesc(ctypes.Structure):
+    _fields_ = [("slc", ctypes.c_void_p), ("N", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("ref_idx", ctypes.c_int32), ("phase", ctypes.c_void_p), ("tcoh", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
+
+
 COV_FP32 = 0  # PLK_COV_FP32
 COV_BF16 = 1  # PLK_COV_BF16
 
@@ -80,6 +86,11 @@ _SIGS = {
     "plk_profile_collect": [_P, ctypes.POINTER(_I)],
     "plk_profile_get": [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
     "plk_phase_link_stack_noalloc": [_P, _I, _I, _I, Window, _I, ctypes.POINTER(Params), _P, _P, _P, _P, _P],
+    "plk_batch_create": [_P, _P, _I, Window, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "plk_batch_run": [_P, _P],
+    "plk_batch_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "plk_batch_destroy": [_P],
+    "plk_tuned_schedule": [_P, _I, Window, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
 }
 EXPORTS = sorted(list(_SIGS) + ["plk_last_error", "plk_mask_words"])
 
@@ -279,6 +290,62 @@ class Context:
         _check(lib().plk_compress(self.h, _ptr(slc), N, int(first_real), H, W, window(win), _ptr(phase),
                                   _ptr(kappa)), self.h)
         return kappa
+
+
+class Batch:
+    """plk_batch: S1-S6 for many independent stacks (uneven N, one window), run
+    as one recorded CUDA graph after a first, tuning, call.  Outputs per stack:
+    phase [N][Ho][Wo], tcoh and status [Ho][Wo] (allocated here)."""
+
+    def __init__(self, ctx: Context, stacks, win, params: Params | None = None, refs=None):
+        self.ctx = ctx
+        self.win = window(win)
+        self.stacks = list(stacks)  # keep the inputs alive
+        refs = refs or [0] * len(self.stacks)
+        self.out = []
+        descs = (StackDesc * len(self.stacks))()
+        for i, (z, ref) in enumerate(zip(self.stacks, refs)):
+            _need(z, torch.complex64, f"stacks[{i}]", ctx.device)
+            N, H, W = z.shape
+            Ho, Wo = output_shape(H, W, self.win)
+            o = {"phase": torch.empty((N, Ho, Wo), device=ctx.device),
+                 "tcoh": torch.empty((Ho, Wo), device=ctx.device),
+                 "status": torch.empty((Ho, Wo), dtype=torch.uint8, device=ctx.device)}
+            self.out.append(o)
+            descs[i] = StackDesc(z.data_ptr(), N, H, W, int(ref), o["phase"].data_ptr(), o["tcoh"].data_ptr(),
+                                 o["status"].data_ptr())
+        p = params if params is not None else default_params()
+        h = ctypes.c_void_p()
+        _check(lib().plk_batch_create(ctx.h, ctypes.cast(descs, ctypes.c_void_p), len(self.stacks), self.win,
+                                      ctypes.byref(p), ctypes.byref(h)), ctx.h)
+        self.h = h
+
+    def run(self):
+        _check(lib().plk_batch_run(self.ctx.h, self.h), self.ctx.h)
+        return self.out
+
+    def info(self) -> dict:
+        g, s, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().plk_batch_info(self.h, ctypes.byref(g), ctypes.byref(s), ctypes.byref(n)))
+        return {"graph_built": g.value, "streams": s.value, "nodes": n.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().plk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tuned_schedule(ctx: Context, N: int, win) -> dict:
+    ty, tx, np_ = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().plk_tuned_schedule(ctx.h, int(N), window(win), ctypes.byref(ty), ctypes.byref(tx),
+                                    ctypes.byref(np_)), ctx.h)
+    return {"cov_tile": (ty.value, tx.value), "emi_lanes": np_.value}
 
 
 class State:
