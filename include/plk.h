@@ -241,6 +241,28 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
                               const plk_params *params, float *phase, float *tcoh,
                               uint8_t *status, uint16_t *shp_count);
 
+/* ----------------------------------------------------------- adjoint */
+
+/* Scratch bytes plk_phase_link_backward needs for this stack and window. */
+plk_status plk_backward_workspace_size(int N, int H, int W, plk_window win, size_t *bytes);
+/* Adjoint of S3-S5 (coherence, Sec. II-A; EMI eigenvector, Sec. III-B;
+ * referenced phase, Sec. II-A) with the SHP masks frozen: for
+ * L = sum_{i,p} dphase[i][p] * phase[i][p], where phase is what
+ * plk_estimate_covariance + plk_phase_link (single-precision solve, same mask,
+ * ref_idx and params) produce, writes dslc [N][H][W] with
+ * dL = Re sum conj(dslc) dz, i.e. dslc = dL/dRe z + j dL/dIm z.
+ * The eigenvector derivative is the first-order perturbation of a simple
+ * eigenvalue (it grows as 1 / eigengap); the coherence is recomputed, not
+ * stored.  slc [N][H][W]; mask as from plk_shp_select; dphase [N][Ho][Wo];
+ * workspace: device memory of plk_backward_workspace_size bytes, owned by
+ * the caller (nothing is allocated).  Pixels without data contribute nothing.
+ * N <= 32.  Errors: EINVAL (bad argument, small workspace), ECUDA.  The paper
+ * states no adjoint. */
+plk_status plk_phase_link_backward(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W, plk_window win,
+                                   const uint64_t *mask, int ref_idx, const plk_params *params,
+                                   const float *dphase, void *workspace, size_t workspace_bytes,
+                                   plk_c64 *dslc);
+
 /* ------------------------------------------------ batches of stacks */
 
 /* One independent stack of a batch: its SLCs and where its outputs go (all

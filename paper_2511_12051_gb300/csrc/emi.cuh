@@ -238,6 +238,10 @@ struct PixelResult {
     float lam;
     int status;
     bool flag;    // the single-precision solve asks for the FP64 re-solve
+    // For the adjoint (single-precision solve): this lane's entry of the unit
+    // eigenvector and whether the EVD fallback produced it.
+    cpx<float> v;
+    bool evd;
 };
 
 constexpr int kPending = 0xFE;  // status of a pixel handed to the FP64 re-solve
@@ -510,6 +514,8 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
 
     out.phase = (float)ph;
     out.tcoh = (float)tcoh;
+    out.v = mk<float>((float)x.x, (float)x.y);
+    out.evd = inv_failed;
 #ifndef PLK_DEBUG_EST
     out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
 #else

@@ -1,0 +1,373 @@
+// Adjoint of S3-S5 (coherence -> EMI eigenvector -> referenced phase) with
+// the SHP masks frozen: for L = sum_{p,i} w_{p,i} phihat_{p,i}, the gradient
+// g(q) with dL = Re sum conj(g) dz over the SLC stack (the convention under
+// which g = dL/dRe z + j dL/dIm z).  The coherence is recomputed here, not
+// stored by the forward pass.
+//
+// Per output pixel p (an NP-lane group, lane r owning row r):
+//   phihat_i = arg(v_i conj(v_ref)):  g_v,i = w_i j v_i / |v_i|^2 (i != ref),
+//     g_v,ref = -(sum_{i != ref} w_i) j v_ref / |v_ref|^2; the common-phase
+//     direction j v carries no gradient (the phases are gauge invariant).
+//   v = unit eigenvector of A for the simple eigenvalue lambda (A = G^-1 o C,
+//     or C itself on the EVD fallback):  dv = -(A - lambda I)^+ dA v, so with
+//     u = (A - lambda I + c v v^H)^-1 (g_v - v v^H g_v)  (u orthogonal to v),
+//     the gradient on A is GA = -u v^H.
+//   A = G^-1 o C:  GC += G^-1 o GA;  R = Re(conj(GA) o C);  GG = -G^-1 R G^-1;
+//     G = (1-beta)|C| + beta I:  GC += (1-beta) GG o C/|C|  (off the diagonal,
+//     which is constant).
+//   C_ik = S_ik / sqrt(S_ii S_kk):  GS_ik = GC_ik / sqrt(S_ii S_kk) (i != k),
+//     GS_ii = -(sum_k P_ik + sum_k P_ki) / (2 S_ii), P = Re(conj(GC) o C).
+//   H_p = GS + GS^H  (Hermitian, stored as the packed upper triangle).
+// Per input pixel q and date i (gather):  g_i(q) = sum over the output
+//   pixels p whose window holds q with the mask bit set of (H_p z(q))_i.
+#include "emi.cuh"
+
+namespace plk {
+
+namespace {
+
+constexpr int kAdjWarps = 2;
+
+// Row of the coherence cached in shared memory, padded (see k_emi.cu).
+template <int NP>
+struct AdjRow {
+    static constexpr bool kPadded = true;
+    const cpx<float> *row;
+    __device__ __forceinline__ cpx<float> operator()(int k) const { return row[k]; }
+    __device__ __forceinline__ void all(cpx<float> (&c)[NP]) const {
+        const uint4 *src = reinterpret_cast<const uint4 *>(row);
+#pragma unroll
+        for (int q = 0; q < NP / 2; ++q) {
+            const uint4 v = src[q];
+            memcpy(&c[2 * q], &v, 16);
+        }
+    }
+};
+
+// Publish every lane's row of an NP x NP matrix to the group's buffer.
+template <int NP, class S>
+__device__ __forceinline__ void publish(const S (&row)[NP], S *mat, int r, unsigned gmask) {
+    __syncwarp(gmask);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) mat[r * NP + k] = row[k];
+    __syncwarp(gmask);
+}
+
+}  // namespace
+
+// Diagonal sums S_ii = sum over the mask of |z_i(q)|^2, one thread per
+// (output pixel, date).
+__global__ void __launch_bounds__(256) k_adj_sdiag(const __grid_constant__ Planes z, int n, const Geom g,
+                                                   const uint64_t *__restrict__ mask, float *__restrict__ Sd) {
+    const long long nout = (long long)g.Ho * g.Wo;
+    const long long total = nout * n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / nout);
+        const long long o = t - (long long)i * nout;
+        const int oy = (int)(o / g.Wo), ox = (int)(o - (long long)oy * g.Wo);
+        const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
+        const uint64_t *mw = mask + o * g.nwords;
+        float s = 0.f;
+        int b = 0;
+        for (int dy = -g.hy; dy <= g.hy; ++dy)
+            for (int dx = -g.hx; dx <= g.hx; ++dx, ++b) {
+                if (!((__ldg(mw + (b >> 6)) >> (b & 63)) & 1ull)) continue;
+                const float2 v = __ldg(z.p[i] + (long long)(cy + dy) * g.W + (cx + dx));
+                s += v.x * v.x + v.y * v.y;
+            }
+        Sd[o * n + i] = s;
+    }
+}
+
+// Per output pixel: H_p from the coherence C (packed), the diagonal sums and
+// the phase weights w [n][npx].  Pixels without data get H_p = 0.
+template <int NP>
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adj_pixel(const float2 *__restrict__ C,
+                                                              const float *__restrict__ Sd, int n, long long npx,
+                                                              int ref, const EmiParams prm,
+                                                              const float *__restrict__ w,
+                                                              float2 *__restrict__ Hout) {
+    constexpr int G = 32 / NP;
+    constexpr int kRowPitch = NP + 2;
+    constexpr int kGrpBuf = 2 * NP + 2;
+    __shared__ __align__(16) cpx<float> sbuf[kAdjWarps][G * kGrpBuf];
+    __shared__ __align__(16) cpx<float> rowcache[kAdjWarps * 32 * kRowPitch];
+    __shared__ __align__(16) cpx<float> mats[kAdjWarps][32 * NP];  // one NP x NP matrix per group
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / NP, r = lane - grp * NP;
+    const int glane0 = grp * NP;
+    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const long long nt = ntri(n);
+    const long long step = (long long)gridDim.x * kAdjWarps * G;
+    cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
+    cpx<float> *cbuf = &sbuf[warp][grp * kGrpBuf];
+    float *rbuf = reinterpret_cast<float *>(cbuf);
+    cpx<float> *cmat = &mats[warp][grp * NP * NP];
+    float *fmat = reinterpret_cast<float *>(cmat);
+    EmiParams q = prm;
+    q.fp64_resolve = 0;  // the adjoint differentiates the single-precision solve
+
+    for (long long base = ((long long)blockIdx.x * kAdjWarps + warp) * G; base < npx; base += step) {
+        const long long p = base + grp;
+        const bool valid = p < npx;
+        const float2 *Cpix = C + (valid ? p : 0) * nt;
+        const bool live = r < n;
+        bool nan = false;
+        if (valid && live) nan = isnan(__ldg(Cpix + packed_index(n, r, r)).x);
+        nan = __any_sync(gmask, nan);
+        if (!valid) continue;
+        if (nan) {
+            if (live)
+                for (int k = r; k < n; ++k) Hout[p * nt + packed_index(n, r, k)] = make_float2(0.f, 0.f);
+            continue;
+        }
+        {
+            const int base_r = r * n - r * (r - 1) / 2 - r;
+            int idx_col = r;
+            cpx<float> v[NP];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                v[k] = mk<float>((!live && k == r) ? 1.f : 0.f, 0.f);
+                if (live && k < n) {
+                    if (k >= r) {
+                        const float2 c = __ldg(Cpix + base_r + k);
+                        v[k] = mk<float>(c.x, c.y);
+                    } else {
+                        const float2 c = __ldg(Cpix + idx_col);
+                        v[k] = mk<float>(c.x, -c.y);
+                        idx_col += n - k - 1;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) myrow[k] = v[k];
+        }
+        __syncwarp(gmask);
+        const AdjRow<NP> ld{myrow};
+        const PixelResult res = emi_solve<NP, float>(ld, r, n, ref, q, cbuf, gmask, glane0, false);
+        const cpx<float> v = live ? res.v : mk<float>(0.f, 0.f);
+
+        // Gradient on v (gauge-free), projected orthogonal to v.
+        const float wr = live ? __ldg(w + (long long)r * npx + p) : 0.f;
+        const float wsum = group_sum<NP, float>(live && r != ref ? wr : 0.f, gmask);
+        const float m2 = norm2(v);
+        const float coef = (r == ref) ? -wsum : wr;
+        cpx<float> gv = (live && m2 > 0.f) ? (coef / m2) * mk<float>(-v.y, v.x) : mk<float>(0.f, 0.f);
+        {
+            const cpx<float> t = conj(v) * gv;
+            const float sx = group_sum<NP, float>(t.x, gmask), sy = group_sum<NP, float>(t.y, gmask);
+            gv = gv - v * mk<float>(sx, sy);
+        }
+
+        // A row (C, or G^-1 o C) and G^-1 row.
+        cpx<float> crow[NP], a[NP];
+        float gi[NP];
+        load_crow<NP, float>(crow, ld, r, n);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float m = mag_t(norm2(crow[k]));
+            if (q.beta != 0.f) m = (1.f - q.beta) * m + ((k == r) ? q.beta : 0.f);
+            gi[k] = m;
+        }
+        if (!res.evd) gj_invert<NP, float, float, true>(gi, rbuf, r, n, gmask, 0.f);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) a[k] = res.evd ? crow[k] : mk<float>(gi[k] * crow[k].x, gi[k] * crow[k].y);
+        // lambda = v^H A v (the eigenvalue the perturbation is about)
+        const cpx<float> av = group_matvec<NP, float>(a, v, cbuf, r, gmask);
+        const float lam = group_sum<NP, float>(live ? (v.x * av.x + v.y * av.y) : 0.f, gmask);
+        // every lane's v
+        cpx<float> vv[NP];
+        cbuf[r] = v;
+        __syncwarp(gmask);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) vv[k] = cbuf[k];
+        __syncwarp(gmask);
+        // u = (A - lambda I + c v v^H)^-1 g_v  (c keeps the deflated matrix well scaled)
+        const float cdef = fmaxf(1.f, fabsf(lam));
+        cpx<float> mrow[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            mrow[k] = a[k] + cdef * (v * conj(vv[k]));
+            if (k == r && live) mrow[k].x -= lam;
+        }
+        gj_invert<NP, float, cpx<float>, false>(mrow, cbuf, r, n, gmask, 0.f);
+        const cpx<float> u = group_matvec<NP, float>(mrow, gv, cbuf, r, gmask);
+
+        // GA = -u v^H (row r), then GC (off the diagonal).
+        cpx<float> gc[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) gc[k] = mk<float>(0.f, 0.f) - u * conj(vv[k]);  // GA for now
+        if (!res.evd) {
+            float R[NP];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) R[k] = gc[k].x * crow[k].x + gc[k].y * crow[k].y;  // Re(conj(GA) C)
+            // T = G^-1 R (row r): sum_j gi[j] R_j.
+            publish<NP, float>(R, fmat, r, gmask);
+            float T[NP];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) T[k] = 0.f;
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+#pragma unroll
+                for (int k = 0; k < NP; ++k) T[k] += gi[j] * fmat[j * NP + k];
+            // GG = -T G^-1 (row r): -sum_j T[j] Ginv_j.
+            publish<NP, float>(gi, fmat, r, gmask);
+            float GG[NP];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) GG[k] = 0.f;
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+#pragma unroll
+                for (int k = 0; k < NP; ++k) GG[k] -= T[j] * fmat[j * NP + k];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float cm2 = norm2(crow[k]);
+                const cpx<float> ph = cm2 > 0.f ? rsqrtf(cm2) * crow[k] : mk<float>(0.f, 0.f);
+                gc[k] = gi[k] * gc[k] + ((1.f - q.beta) * GG[k]) * ph;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+            if (k == r || k >= n || !live) gc[k] = mk<float>(0.f, 0.f);
+
+        // C -> S.
+        const float sr = live ? __ldg(Sd + p * n + r) : 0.f;
+        const float rsr = sr > 0.f ? rsqrtf(sr) : 0.f;
+        float rs[NP];
+        rbuf[r] = rsr;
+        __syncwarp(gmask);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) rs[k] = rbuf[k];
+        __syncwarp(gmask);
+        float P[NP];
+        float rowsum = 0.f;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            P[k] = gc[k].x * crow[k].x + gc[k].y * crow[k].y;
+            rowsum += P[k];
+        }
+        publish<NP, float>(P, fmat, r, gmask);
+        float colsum = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) colsum += fmat[i * NP + r];
+        cpx<float> gs[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) gs[k] = (rsr * rs[k]) * gc[k];
+        if (live && sr > 0.f) gs[r] = mk<float>(-(rowsum + colsum) / (2.f * sr), 0.f);
+
+        // H = GS + GS^H, packed upper triangle.
+        publish<NP, cpx<float>>(gs, cmat, r, gmask);
+        if (live) {
+            float2 *Hp = Hout + p * nt;
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                if (k >= r && k < n) {
+                    const cpx<float> h = gs[k] + conj(cmat[k * NP + r]);
+                    Hp[packed_index(n, r, k)] = make_float2(h.x, h.y);
+                }
+        }
+        __syncwarp(gmask);
+    }
+}
+
+// Per (input pixel q, date i): g_i(q) = sum over the output pixels p whose
+// window holds q, with q's mask bit set, of sum_k H_p,ik z_k(q).  NT >= n.
+template <int NT>
+__global__ void __launch_bounds__(256) k_adj_gather(const __grid_constant__ Planes z, int n, const Geom g,
+                                                    const uint64_t *__restrict__ mask,
+                                                    const float2 *__restrict__ H, float2 *__restrict__ grad) {
+    const long long npix = (long long)g.H * g.W;
+    const long long total = npix * n;
+    const long long nt = ntri(n);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / npix);
+        const long long qi = t - (long long)i * npix;
+        const int qy = (int)(qi / g.W), qx = (int)(qi - (long long)qy * g.W);
+        cpx<float> zq[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+            const float2 v = k < n ? __ldg(z.p[k] + qi) : make_float2(0.f, 0.f);
+            zq[k] = mk<float>(v.x, v.y);
+        }
+        // output rows/columns whose window centre lies within hy/hx of q
+        const int oy_lo = max(0, (qy - g.hy - g.sy / 2 + g.sy - 1) / g.sy);
+        const int oy_hi = min(g.Ho - 1, (qy + g.hy - g.sy / 2) >= 0 ? (qy + g.hy - g.sy / 2) / g.sy : -1);
+        const int ox_lo = max(0, (qx - g.hx - g.sx / 2 + g.sx - 1) / g.sx);
+        const int ox_hi = min(g.Wo - 1, (qx + g.hx - g.sx / 2) >= 0 ? (qx + g.hx - g.sx / 2) / g.sx : -1);
+        cpx<float> acc = mk<float>(0.f, 0.f);
+        for (int oy = oy_lo; oy <= oy_hi; ++oy) {
+            const int dy = qy - (oy * g.sy + g.sy / 2);
+            if (dy < -g.hy || dy > g.hy) continue;
+            for (int ox = ox_lo; ox <= ox_hi; ++ox) {
+                const int dx = qx - (ox * g.sx + g.sx / 2);
+                if (dx < -g.hx || dx > g.hx) continue;
+                const long long o = (long long)oy * g.Wo + ox;
+                const int b = (dy + g.hy) * g.wx + (dx + g.hx);
+                if (!((__ldg(mask + o * g.nwords + (b >> 6)) >> (b & 63)) & 1ull)) continue;
+                const float2 *Hp = H + o * nt;
+#pragma unroll
+                for (int k = 0; k < NT; ++k) {
+                    if (k >= n) break;
+                    // H_ik from the packed upper triangle (H Hermitian)
+                    const float2 h = __ldg(Hp + (i <= k ? packed_index(n, i, k) : packed_index(n, k, i)));
+                    const cpx<float> hik = i <= k ? mk<float>(h.x, h.y) : mk<float>(h.x, -h.y);
+                    acc = cfma(hik, zq[k], acc);
+                }
+            }
+        }
+        grad[(long long)i * npix + qi] = make_float2(acc.x, acc.y);
+    }
+}
+
+static int adj_grid(long long work) {
+    long long blocks = (work + 255) / 256;
+    const long long cap = (long long)device_sm_count() * 8;
+    return (int)std::max<long long>(1, std::min(blocks, cap));
+}
+
+template <int NP>
+static cudaError_t run_adj_pixel(const float2 *C, const float *Sd, int n, long long npx, int ref,
+                                 const EmiParams &prm, const float *w, float2 *H, cudaStream_t s) {
+    constexpr int G = 32 / NP;
+    long long blocks = ((npx + G - 1) / G + kAdjWarps - 1) / kAdjWarps;
+    const long long cap = (long long)device_sm_count() * 16;
+    blocks = std::max<long long>(1, std::min(blocks, cap));
+    k_adj_pixel<NP><<<(unsigned)blocks, kAdjWarps * 32, 0, s>>>(C, Sd, n, npx, ref, prm, w, H);
+    return cudaGetLastError();
+}
+
+// Workspace layout: C [npx][ntri], H [npx][ntri], Sd [npx][n] (256-byte aligned parts).
+size_t adjoint_workspace_bytes(int n, const Geom &g) {
+    const long long npx = (long long)g.Ho * g.Wo;
+    auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    return 2 * a256((size_t)npx * ntri(n) * sizeof(float2)) + a256((size_t)npx * n * sizeof(float));
+}
+
+cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
+                           const EmiParams &prm, const float *dphase, void *workspace, float2 *grad,
+                           cudaStream_t s) {
+    const long long npx = (long long)g.Ho * g.Wo, npix = (long long)g.H * g.W;
+    auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    char *ws = static_cast<char *>(workspace);
+    float2 *C = reinterpret_cast<float2 *>(ws);
+    float2 *H = reinterpret_cast<float2 *>(ws + a256((size_t)npx * ntri(n) * sizeof(float2)));
+    float *Sd = reinterpret_cast<float *>(ws + 2 * a256((size_t)npx * ntri(n) * sizeof(float2)));
+    if (npx == 0) return cudaMemsetAsync(grad, 0, (size_t)npix * n * sizeof(float2), s);
+    cudaError_t e = launch_covariance(z, n, g, mask, C, s);  // recomputed, not stored by the forward pass
+    if (e != cudaSuccess) return e;
+    k_adj_sdiag<<<adj_grid(npx * n), 256, 0, s>>>(z, n, g, mask, Sd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n <= 8) e = run_adj_pixel<8>(C, Sd, n, npx, ref, prm, dphase, H, s);
+    else if (n <= 16) e = run_adj_pixel<16>(C, Sd, n, npx, ref, prm, dphase, H, s);
+    else e = run_adj_pixel<32>(C, Sd, n, npx, ref, prm, dphase, H, s);
+    if (e != cudaSuccess) return e;
+    const int grid = adj_grid(npix * n);
+    if (n <= 8) k_adj_gather<8><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
+    else if (n <= 16) k_adj_gather<16><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
+    else k_adj_gather<32><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace plk

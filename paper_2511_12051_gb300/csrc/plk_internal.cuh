@@ -83,6 +83,12 @@ cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &
 
 int device_sm_count();
 // Nonzero if a bounded device-side wait gave up since the last call (then cleared).
+// Adjoint of S3-S5 (masks frozen): scratch bytes and the launch sequence
+// (coherence recomputed into the workspace).
+size_t adjoint_workspace_bytes(int n, const Geom &g);
+cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
+                           const EmiParams &prm, const float *dphase, void *workspace, float2 *grad,
+                           cudaStream_t s);
 int read_and_clear_wait_timeout();
 cudaError_t launch_wait_selftest(cudaStream_t s);
 // Text returned by plk_last_error(NULL) on this thread.

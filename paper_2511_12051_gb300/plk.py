@@ -86,6 +86,9 @@ _SIGS = {
     "plk_profile_collect": [_P, ctypes.POINTER(_I)],
     "plk_profile_get": [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
     "plk_phase_link_stack_noalloc": [_P, _I, _I, _I, Window, _I, ctypes.POINTER(Params), _P, _P, _P, _P, _P],
+    "plk_backward_workspace_size": [_I, _I, _I, Window, ctypes.POINTER(ctypes.c_size_t)],
+    "plk_phase_link_backward": [_P, _P, _I, _I, _I, Window, _P, _I, ctypes.POINTER(Params), _P, _P,
+                                ctypes.c_size_t, _P],
     "plk_batch_create": [_P, _P, _I, Window, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "plk_batch_run": [_P, _P],
     "plk_batch_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -279,6 +282,25 @@ class Context:
                                     _ptr(lam), _ptr(status)), self.h)
         return {"phase": phase, "tcoh": tcoh, "lam": lam, "status": status}
 
+    def phase_link_backward(self, slc: torch.Tensor, win, mask: torch.Tensor, ref: int, dphase: torch.Tensor,
+                            params: Params | None = None, dslc: torch.Tensor | None = None) -> torch.Tensor:
+        """Adjoint of coherence -> EMI -> referenced phase (mask frozen): the
+        gradient dL/dRe z + j dL/dIm z of L = sum(dphase * phase)."""
+        _need(slc, torch.complex64, "slc", self.device)
+        _need(mask, torch.int64, "mask", self.device)
+        _need(dphase, torch.float32, "dphase", self.device)
+        N, H, W = slc.shape
+        w = window(win)
+        nbytes = ctypes.c_size_t()
+        _check(lib().plk_backward_workspace_size(N, H, W, w, ctypes.byref(nbytes)))
+        ws = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=self.device)
+        if dslc is None:
+            dslc = torch.empty_like(slc)
+        p = params if params is not None else default_params()
+        _check(lib().plk_phase_link_backward(self.h, _ptr(slc), N, H, W, w, _ptr(mask), int(ref), ctypes.byref(p),
+                                             _ptr(dphase), _ptr(ws), nbytes.value, _ptr(dslc)), self.h)
+        return dslc
+
     def compress(self, slc: torch.Tensor, first_real: int, win, phase: torch.Tensor,
                  kappa: torch.Tensor | None = None):
         _need(slc, torch.complex64, "slc", self.device)
@@ -290,6 +312,30 @@ class Context:
         _check(lib().plk_compress(self.h, _ptr(slc), N, int(first_real), H, W, window(win), _ptr(phase),
                                   _ptr(kappa)), self.h)
         return kappa
+
+
+class PhaseLinkFn(torch.autograd.Function):
+    """phase = coherence -> EMI -> referenced phase of a stack, with the SHP
+    mask given (frozen); differentiable in the stack.  The gradient follows
+    torch's convention for complex inputs (dL/dRe z + j dL/dIm z for real L)."""
+
+    @staticmethod
+    def forward(fctx, slc, mask, win, ref, plk_ctx, params=None):
+        C = plk_ctx.estimate_covariance(slc, win, mask)
+        N = slc.shape[0]
+        p = params if params is not None else default_params()
+        p = Params.from_buffer_copy(p)
+        p.fp64_resolve = 0  # the adjoint differentiates the single-precision solve
+        out = plk_ctx.phase_link(C, N, ref, p)
+        fctx.save_for_backward(slc, mask)
+        fctx.win, fctx.ref, fctx.plk_ctx, fctx.params = win, ref, plk_ctx, p
+        return out["phase"]
+
+    @staticmethod
+    def backward(fctx, dphase):
+        slc, mask = fctx.saved_tensors
+        g = fctx.plk_ctx.phase_link_backward(slc, fctx.win, mask, fctx.ref, dphase.contiguous().float(), fctx.params)
+        return g, None, None, None, None, None
 
 
 class Batch:
