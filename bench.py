@@ -266,6 +266,74 @@ def run_batch(args, rank: int, world: int, local: int):
     return 0
 
 
+def run_adjoint(args, rank: int, world: int, local: int):
+    """Adjoint workload: N=20 x 1024x1024 (cfg0-type coherence and ramp), 11x5
+    window, stride 1, masks frozen; forward = coherence + EMI (single-precision
+    solve), backward = plk_phase_link_backward of sum(w * phase), w ~ U(-1, 1)."""
+    import torch
+    from paper_2511_12051_gb300 import build, synth, plk
+    from paper_2511_12051_gb300 import dist as pdist
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    win = (5, 11, 1, 1)
+    spec = synth.config_spec(4, seed=pdist.unit_seed(4, rank))
+    z = synth.generate(spec, device=dev)
+    N = z.shape[0]
+    stream = torch.cuda.Stream(dev)
+    ctx = plk.Context(dev, stream)
+    with torch.cuda.stream(stream):
+        P, _ = ctx.amp_stats(z)
+        mask, _ = ctx.shp_select(P, N, win, 1e-3)
+        prm = plk.default_params(fp64_resolve=0)
+        C = ctx.estimate_covariance(z, win, mask)
+        out = ctx.phase_link(C, N, 0, prm)
+        g = torch.Generator(device=dev).manual_seed(4)
+        w = torch.rand(out["phase"].shape, device=dev, generator=g) * 2 - 1
+        dz = ctx.phase_link_backward(z, win, mask, 0, w, prm)
+    torch.cuda.synchronize(dev)
+
+    def fwd():
+        ctx.estimate_covariance(z, win, mask, C=C)
+        ctx.phase_link(C, N, 0, prm)
+
+    def bwd():
+        ctx.phase_link_backward(z, win, mask, 0, w, prm, dslc=dz)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_f, ms_b = timed(fwd), timed(bwd)
+    ctx.profile(True)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            bwd()
+    torch.cuda.synchronize(dev)
+    stages = {kk: v[0] / 2 for kk, v in ctx.profile_collect().items()}
+    ctx.profile(False)
+    npx = out["status"].numel()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": npx * world / (ms_b / 1e3), "unit": "output px/s (backward)", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adjoint: N=20 x 1024x1024, 11x5 window, stride 1, masks frozen, "
+                                   "L = sum(w * phase), w ~ U(-1, 1)", "output_px_per_gpu": npx},
+            "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
+            "backward_stages_ms": stages,
+            "forward_px_per_s": npx * world / (ms_f / 1e3)}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -280,8 +348,9 @@ def main():
     ap.add_argument("--cov-precision", default="fp32", choices=["fp32", "bf16"],
                     help="coherence arithmetic of the timed step (fp32: the plain path)")
     ap.add_argument("--no-modes", action="store_true", help="skip timing the bfloat16-coherence mode beside it")
-    ap.add_argument("--workload", default="burst", choices=["burst", "batch"],
-                    help="burst: the headline mini-stack step; batch: 64 uneven stacks in one recorded graph")
+    ap.add_argument("--workload", default="burst", choices=["burst", "batch", "adjoint"],
+                    help="burst: the headline mini-stack step; batch: 64 uneven stacks in one recorded graph; "
+                         "adjoint: forward and backward of the phase linking on N=20 x 1024x1024")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -293,6 +362,8 @@ def main():
         return run_reference(args, rank)
     if args.workload == "batch":
         return run_batch(args, rank, world, local)
+    if args.workload == "adjoint":
+        return run_adjoint(args, rank, world, local)
 
     import torch
     import torch.distributed as dist

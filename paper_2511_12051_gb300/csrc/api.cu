@@ -435,10 +435,8 @@ plk_status plk_phase_link_backward(plk_ctx *ctx, const plk_c64 *slc, int N, int 
     DeviceGuard dg(ctx->device);
     Planes z{};
     for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
-    ctx->prof.begin("backward", ctx->stream);
     cudaError_t e = plk::launch_adjoint(z, N, g, mask, ref_idx, prm, dphase, workspace,
-                                        reinterpret_cast<float2 *>(dslc), ctx->stream);
-    ctx->prof.end(ctx->stream);
+                                        reinterpret_cast<float2 *>(dslc), ctx->stream, &ctx->prof);
     if (e == cudaErrorInvalidConfiguration)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_phase_link_backward: window with N=%d exceeds shared memory", N);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_phase_link_backward");

@@ -20,6 +20,8 @@
 //   H_p = GS + GS^H  (Hermitian, stored as the packed upper triangle).
 // Per input pixel q and date i (gather):  g_i(q) = sum over the output
 //   pixels p whose window holds q with the mask bit set of (H_p z(q))_i.
+#include <algorithm>
+
 #include "emi.cuh"
 
 namespace plk {
@@ -273,6 +275,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_pixel(const float2 *__re
 
 // Per (input pixel q, date i): g_i(q) = sum over the output pixels p whose
 // window holds q, with q's mask bit set, of sum_k H_p,ik z_k(q).  NT >= n.
+// The date index runs fastest across threads: a warp covers one or two
+// pixels, so its loads of H_p rows fall on one or two packed matrices and the
+// loads of z(q) are broadcasts.
 template <int NT>
 __global__ void __launch_bounds__(256) k_adj_gather(const __grid_constant__ Planes z, int n, const Geom g,
                                                     const uint64_t *__restrict__ mask,
@@ -282,8 +287,8 @@ __global__ void __launch_bounds__(256) k_adj_gather(const __grid_constant__ Plan
     const long long nt = ntri(n);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t / npix);
-        const long long qi = t - (long long)i * npix;
+        const long long qi = t / n;
+        const int i = (int)(t - qi * n);
         const int qy = (int)(qi / g.W), qx = (int)(qi - (long long)qy * g.W);
         cpx<float> zq[NT];
 #pragma unroll
@@ -321,6 +326,112 @@ __global__ void __launch_bounds__(256) k_adj_gather(const __grid_constant__ Plan
     }
 }
 
+// Tiled scatter of the same sum: a CTA owns a TY x TX tile of output pixels,
+// stages the z of the input region their windows cover and a region-sized
+// accumulator in shared memory; item (pixel s, row i) loads row i of H_p once
+// and adds (H_p z(q))_i into the accumulator for every accepted look q; the
+// accumulator is then added into the gradient (tiles overlap by the window
+// halo).  H is read once; the sums are shared-memory atomics, so the order of
+// additions (and the last bits of the result) may vary from run to run.
+struct AdjTile {
+    int TY, TX, RY, RX, L;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(256) k_adj_scatter(const __grid_constant__ Planes z, int n, const Geom g,
+                                                     const uint64_t *__restrict__ mask, const float2 *__restrict__ H,
+                                                     float2 *__restrict__ grad, const AdjTile t, long long ntiles,
+                                                     int tilesY) {
+    extern __shared__ __align__(16) float2 sm[];
+    const int npr = t.RY * t.RX;
+    float2 *zreg = sm;                                         // [npr][n]
+    float2 *acc = sm + (size_t)npr * n;                        // [npr][n]
+    int *lkoff = reinterpret_cast<int *>(acc + (size_t)npr * n);  // [L]
+    const long long nt = ntri(n);
+    const long long npix = (long long)g.H * g.W;
+    for (int l = threadIdx.x; l < t.L; l += blockDim.x) lkoff[l] = (l / g.wx) * t.RX + (l % g.wx);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ty0 = (int)(tile % tilesY) * t.TY, tx0 = (int)(tile / tilesY) * t.TX;
+        const int y0 = ty0 * g.sy + g.sy / 2 - g.hy, x0 = tx0 * g.sx + g.sx / 2 - g.hx;
+        __syncthreads();  // previous tile done with the buffers (and the look table written)
+        for (int idx = threadIdx.x; idx < npr * n; idx += blockDim.x) {
+            const int d = idx / npr, pr = idx - d * npr;
+            const int y = y0 + pr / t.RX, x = x0 + pr % t.RX;
+            float2 v = make_float2(0.f, 0.f);
+            if (y >= 0 && y < g.H && x >= 0 && x < g.W) v = __ldg(z.p[d] + (long long)y * g.W + x);
+            zreg[pr * n + d] = v;
+            acc[pr * n + d] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int items = t.TY * t.TX * n;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int s = it / n, i = it - s * n;
+            const int tx = s / t.TY, ty = s - tx * t.TY;
+            const int oy = ty0 + ty, ox = tx0 + tx;
+            if (oy >= g.Ho || ox >= g.Wo) continue;
+            const long long o = (long long)oy * g.Wo + ox;
+            const float2 *Hp = H + o * nt;
+            cpx<float> hrow[NT];
+#pragma unroll
+            for (int k = 0; k < NT; ++k) {
+                hrow[k] = mk<float>(0.f, 0.f);
+                if (k < n) {
+                    const float2 h = __ldg(Hp + (i <= k ? packed_index(n, i, k) : packed_index(n, k, i)));
+                    hrow[k] = i <= k ? mk<float>(h.x, h.y) : mk<float>(h.x, -h.y);
+                }
+            }
+            const uint64_t *mw = mask + o * g.nwords;
+            const int corner = ty * g.sy * t.RX + tx * g.sx;
+            for (int w0 = 0; w0 < t.L; w0 += 64) {
+                uint64_t bits = __ldg(mw + (w0 >> 6));
+                if (t.L - w0 < 64) bits &= (1ull << (t.L - w0)) - 1ull;  // only the window's looks
+                while (bits) {
+                    const int l = w0 + __ffsll((long long)bits) - 1;
+                    bits &= bits - 1;
+                    const float2 *zq = zreg + (size_t)(corner + lkoff[l]) * n;
+                    cpx<float> a = mk<float>(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < NT; ++k) {
+                        if (k >= n) break;
+                        const float2 zz = zq[k];
+                        a = cfma(hrow[k], mk<float>(zz.x, zz.y), a);
+                    }
+                    float2 *dst = acc + (size_t)(corner + lkoff[l]) * n + i;
+                    atomicAdd(&dst->x, a.x);
+                    atomicAdd(&dst->y, a.y);
+                }
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < npr * n; idx += blockDim.x) {
+            const int d = idx / npr, pr = idx - d * npr;
+            const int y = y0 + pr / t.RX, x = x0 + pr % t.RX;
+            if (y < 0 || y >= g.H || x < 0 || x >= g.W) continue;
+            const float2 v = acc[pr * n + d];
+            if (v.x == 0.f && v.y == 0.f) continue;
+            float2 *dst = grad + (long long)d * npix + (long long)y * g.W + x;
+            atomicAdd(&dst->x, v.x);
+            atomicAdd(&dst->y, v.y);
+        }
+    }
+}
+
+// Tile for the scatter: the most output pixels whose region (z and
+// accumulator, n samples each) fits the budget.
+static AdjTile adj_tile(int n, const Geom &g, size_t budget) {
+    AdjTile best{0, 0, 0, 0, g.wy * g.wx};
+    for (int TY = 1; TY <= 32; ++TY)
+        for (int TX = 1; TX <= 64; ++TX) {
+            AdjTile c{TY, TX, (TY - 1) * g.sy + g.wy, (TX - 1) * g.sx + g.wx, g.wy * g.wx};
+            const size_t sm = (size_t)c.RY * c.RX * n * 2 * sizeof(float2) + (size_t)c.L * sizeof(int);
+            if (sm > budget) continue;
+            if (TY * TX > best.TY * best.TX ||
+                (TY * TX == best.TY * best.TX && c.RY * c.RX < best.RY * best.RX))
+                best = c;
+        }
+    return best;
+}
+
 static int adj_grid(long long work) {
     long long blocks = (work + 255) / 256;
     const long long cap = (long long)device_sm_count() * 8;
@@ -347,7 +458,7 @@ size_t adjoint_workspace_bytes(int n, const Geom &g) {
 
 cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
                            const EmiParams &prm, const float *dphase, void *workspace, float2 *grad,
-                           cudaStream_t s) {
+                           cudaStream_t s, Prof *prof) {
     const long long npx = (long long)g.Ho * g.Wo, npix = (long long)g.H * g.W;
     auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
     char *ws = static_cast<char *>(workspace);
@@ -355,19 +466,49 @@ cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t
     float2 *H = reinterpret_cast<float2 *>(ws + a256((size_t)npx * ntri(n) * sizeof(float2)));
     float *Sd = reinterpret_cast<float *>(ws + 2 * a256((size_t)npx * ntri(n) * sizeof(float2)));
     if (npx == 0) return cudaMemsetAsync(grad, 0, (size_t)npix * n * sizeof(float2), s);
+    if (prof) prof->begin("adjoint_covariance", s);
     cudaError_t e = launch_covariance(z, n, g, mask, C, s);  // recomputed, not stored by the forward pass
+    if (prof) prof->end(s);
     if (e != cudaSuccess) return e;
+    if (prof) prof->begin("adjoint_pixel", s);
     k_adj_sdiag<<<adj_grid(npx * n), 256, 0, s>>>(z, n, g, mask, Sd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n <= 8) e = run_adj_pixel<8>(C, Sd, n, npx, ref, prm, dphase, H, s);
     else if (n <= 16) e = run_adj_pixel<16>(C, Sd, n, npx, ref, prm, dphase, H, s);
     else e = run_adj_pixel<32>(C, Sd, n, npx, ref, prm, dphase, H, s);
+    if (prof) prof->end(s);
     if (e != cudaSuccess) return e;
-    const int grid = adj_grid(npix * n);
-    if (n <= 8) k_adj_gather<8><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
-    else if (n <= 16) k_adj_gather<16><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
-    else k_adj_gather<32><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
-    return cudaGetLastError();
+    if (prof) prof->begin("adjoint_gather", s);
+    const size_t kBudget = 150 * 1024;
+    const AdjTile t = adj_tile(n, g, kBudget);
+    if (t.TY > 0) {
+        // tiled scatter (H read once)
+        const size_t smem = (size_t)t.RY * t.RX * n * 2 * sizeof(float2) + (size_t)t.L * sizeof(int);
+        e = cudaMemsetAsync(grad, 0, (size_t)npix * n * sizeof(float2), s);
+        if (e != cudaSuccess) return e;
+        const int tilesY = (g.Ho + t.TY - 1) / t.TY;
+        const long long ntiles = (long long)tilesY * ((g.Wo + t.TX - 1) / t.TX);
+        const long long gridT = std::min<long long>(ntiles, (long long)device_sm_count() * 2);
+        if (n <= 8) {
+            cudaFuncSetAttribute(k_adj_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBudget);
+            k_adj_scatter<8><<<(unsigned)gridT, 256, smem, s>>>(z, n, g, mask, H, grad, t, ntiles, tilesY);
+        } else if (n <= 16) {
+            cudaFuncSetAttribute(k_adj_scatter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBudget);
+            k_adj_scatter<16><<<(unsigned)gridT, 256, smem, s>>>(z, n, g, mask, H, grad, t, ntiles, tilesY);
+        } else {
+            cudaFuncSetAttribute(k_adj_scatter<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBudget);
+            k_adj_scatter<32><<<(unsigned)gridT, 256, smem, s>>>(z, n, g, mask, H, grad, t, ntiles, tilesY);
+        }
+    } else {
+        // window too large for a shared-memory region: per-element gather
+        const int grid = adj_grid(npix * n);
+        if (n <= 8) k_adj_gather<8><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
+        else if (n <= 16) k_adj_gather<16><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
+        else k_adj_gather<32><<<grid, 256, 0, s>>>(z, n, g, mask, H, grad);
+    }
+    e = cudaGetLastError();
+    if (prof) prof->end(s);
+    return e;
 }
 
 }  // namespace plk

@@ -88,7 +88,7 @@ int device_sm_count();
 size_t adjoint_workspace_bytes(int n, const Geom &g);
 cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
                            const EmiParams &prm, const float *dphase, void *workspace, float2 *grad,
-                           cudaStream_t s);
+                           cudaStream_t s, Prof *prof = nullptr);
 int read_and_clear_wait_timeout();
 cudaError_t launch_wait_selftest(cudaStream_t s);
 // Text returned by plk_last_error(NULL) on this thread.

@@ -117,7 +117,8 @@ def test_adjoint_matches_library_finite_differences_and_autograd(ctx, plk):
     (ph * wg).sum().backward()
     g_auto = to_np(zr.grad)
     g = gpu_grad(ctx, z, m, win, ref, w)
-    assert np.allclose(g_auto, g, rtol=0, atol=0)
+    # same computation; the scatter's shared-memory sums may add in another order
+    assert np.allclose(g_auto, g, rtol=1e-5, atol=1e-6 * np.abs(g).max())
 
     def loss(zz):
         with torch.no_grad():
