@@ -85,8 +85,23 @@ typedef struct plk_params {
     int32_t cov_precision; /* coherence arithmetic (S3): PLK_COV_FP32 (default) or
                               PLK_COV_BF16 (samples rounded to bfloat16, sums in
                               single precision on the tensor cores; N <= 32) */
-    int32_t reserved[2];
+    int32_t ref_scheme;    /* mini-stack reference scheme of plk_ministack_step:
+                              PLK_REF_FIRST (default) or PLK_REF_LAST_REAL */
+    int32_t reserved[1];
 } plk_params;
+
+/* Mini-stack reference schemes (plk_params.ref_scheme).  Both link each
+ * mini-stack with the newest compressed SLC (or the first real SLC when there
+ * is none) as reference.  PLK_REF_FIRST (Sec. II-B, Fig. 1): the new
+ * compressed SLC is formed on the linked phases as they are, so every one
+ * carries the phase of the archive's first date and all outputs are relative
+ * to it.  PLK_REF_LAST_REAL (Sec. IV; Supplement, "Compressed SLC strategy
+ * for separate batched processing"): the new compressed SLC is formed on the
+ * phases re-referenced to the mini-stack's last real SLC, so it carries that
+ * date's phase and the next mini-stack's outputs are short-baseline
+ * interferograms relative to it. */
+#define PLK_REF_FIRST 0
+#define PLK_REF_LAST_REAL 1
 
 /* Coherence precision modes (plk_params.cov_precision, plk_estimate_covariance). */
 #define PLK_COV_FP32 0
@@ -234,7 +249,9 @@ plk_status plk_state_load(plk_ctx *ctx, const char *path, int M_max, plk_state *
  * EMI with reference = the newest compressed SLC (or the first new SLC on the
  * first step); gamma_t; compress the new SLCs into a new kappa and push it
  * (dropping the oldest beyond K_max).  Outputs for the real dates only:
- * phase [M][Ho][Wo] relative to the first date of the archive, tcoh [Ho][Wo],
+ * phase [M][Ho][Wo] relative to the first date of the archive (PLK_REF_FIRST)
+ * or to the previous mini-stack's last real date (PLK_REF_LAST_REAL; the
+ * first date on the first step), tcoh [Ho][Wo],
  * status [Ho][Wo]; shp_count [Ho][Wo] may be NULL.  1 <= M <= M_max and
  * M + (compressed SLCs held) >= 2.  params NULL = defaults. */
 plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,

@@ -15,6 +15,12 @@ Each step, for new real SLCs z_1..z_M:
      kappa into the ring.
 The phases returned for the real dates are relative to the first date of the
 archive, because every kappa inherits the reference phase of the one before.
+
+scheme="last" (the production variant of Sec. IV and the Supplement's
+"Compressed SLC strategy for separate batched processing"): step 6 forms kappa
+on the linked phases re-referenced to the mini-stack's last real SLC
+(phase_i - phase_last), so kappa carries that date's phase and the next
+mini-stack's phases are relative to it.
 """
 from __future__ import annotations
 
@@ -24,14 +30,17 @@ from . import amp_stats, compress, covariance, glrt_threshold, ntri, phase_link,
 
 
 def ministack(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, n_eff: int,
-              alpha: float, ref: int, beta: float = 0.0, cond: bool = False) -> dict:
+              alpha: float, ref: int, beta: float = 0.0, cond: bool = False, scheme: str = "first") -> dict:
     """One mini-stack through S2-S7 with statistics already merged."""
     N = z.shape[0]
     c = glrt_threshold(alpha, n_eff)
     mask, count = shp_select(sum_pow, window, np.float32(c))
     C = covariance(z, window, mask)
     out = phase_link(C, N, ref, beta, cond=cond)
-    kappa = compress(z, first_real, window, out["phase"])
+    ph = out["phase"]
+    if scheme == "last":
+        ph = ph - ph[N - 1][None]  # re-referenced to the last real SLC
+    kappa = compress(z, first_real, window, ph)
     out.update(mask=mask, count=count, C=C, kappa=kappa, c=c)
     return out
 
@@ -40,7 +49,9 @@ class OracleChain:
     """Sequential processing state: kappa ring, merged power sums, image count."""
 
     def __init__(self, H: int, W: int, window, K_max: int, alpha: float = 1e-3, beta: float = 0.0,
-                 kappa_dtype=np.complex128):
+                 kappa_dtype=np.complex128, scheme: str = "first"):
+        assert scheme in ("first", "last")
+        self.scheme = scheme
         # kappa_dtype=np.complex64 stores each compressed SLC rounded to the
         # single-precision complex samples a stored SLC has (the form the GPU
         # state keeps), so both sides can start a step from identical inputs.
@@ -64,7 +75,7 @@ class OracleChain:
         parts.append(new_slc.astype(np.complex128))
         z = np.concatenate(parts, axis=0)
         ref = K - 1 if K > 0 else 0
-        out = ministack(z, K, self.window, self.sum_pow, self.n, self.alpha, ref, self.beta, cond)
+        out = ministack(z, K, self.window, self.sum_pow, self.n, self.alpha, ref, self.beta, cond, self.scheme)
         self.ring.append(out["kappa"].astype(self.kappa_dtype).astype(np.complex128))
         if len(self.ring) > self.K_max:
             self.ring.pop(0)

@@ -111,16 +111,18 @@ using plk::Geom;
 using plk::Planes;
 
 plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
-                                  int *cov_precision) {
+                                  int *cov_precision, int *ref_scheme) {
     out->work = ctx->work;
     plk_params p;
     if (params) p = *params;
     else plk_default_params(&p);
     if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
         !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0) ||
-        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16))
+        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16) ||
+        (p.ref_scheme != PLK_REF_FIRST && p.ref_scheme != PLK_REF_LAST_REAL))
         return fail(ctx, PLK_EINVAL, "bad plk_params");
     if (cov_precision) *cov_precision = p.cov_precision;
+    if (ref_scheme) *ref_scheme = p.ref_scheme;
     out->beta = p.beta;
     out->mu = p.mu;
     out->tol = p.tol;
@@ -630,8 +632,8 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     if (st->device != ctx->device) return fail(ctx, PLK_EINVAL, "plk_ministack_step: state on another device");
     plk::EmiParams prm;
     double alpha;
-    int cov_precision = PLK_COV_FP32;
-    plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision);
+    int cov_precision = PLK_COV_FP32, ref_scheme = PLK_REF_FIRST;
+    plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision, &ref_scheme);
     if (ps != PLK_OK) return ps;
     if (cov_precision == PLK_COV_BF16 && st->K_used + M > 32)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: bfloat16 coherence needs N <= 32");
@@ -688,7 +690,9 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
         if (K < st->K_max) slot = (st->head + K) % st->K_max;
         else slot = st->head;
         ctx->prof.begin("compress", s);
-        e = plk::launch_compress(z, N, K, g, st->phase_all, st->ring[slot], s);
+        // PLK_REF_LAST_REAL: the new compressed SLC carries the last real date's phase.
+        e = plk::launch_compress(z, N, K, g, st->phase_all, st->ring[slot], s,
+                                 ref_scheme == PLK_REF_LAST_REAL ? N - 1 : -1);
         ctx->prof.end(s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: compress");
         if (K < st->K_max) st->K_used = K + 1;

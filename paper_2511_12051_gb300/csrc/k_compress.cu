@@ -1,6 +1,7 @@
 // S7. Compressed SLC (Sec. II-B): kappa = zeta^H z over the real SLCs, each
 // full-resolution pixel using the linked phases of the output cell whose
-// decimation block contains it (the last cell row/column also takes the rows
+// decimation block contains it (optionally re-referenced to one date, whose
+// phase is subtracted: the last-real-SLC scheme) (the last cell row/column also takes the rows
 // and columns beyond the output grid).
 //
 // A block owns one output row's decimation rows (sy rows, or the remainder for
@@ -21,7 +22,8 @@ static int max_cells(int sx) { return kCompressCols / sx + 2; }
 
 __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constant__ Planes z, int n, int first_real,
                                                            const Geom g, const float *__restrict__ phase,
-                                                           float2 *__restrict__ kappa, int nchunk) {
+                                                           float2 *__restrict__ kappa, int nchunk,
+                                                           int shift_date) {
     extern __shared__ float2 ph[];  // (n - first_real) x ncell phasors, date-major
     const long long nout = (long long)g.Ho * g.Wo;
     const int nr = n - first_real;
@@ -36,7 +38,10 @@ __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constan
         __syncthreads();  // the previous block's phasors are no longer read
         for (int idx = threadIdx.x; idx < nr * ncell; idx += blockDim.x) {
             const int i = idx / ncell, c = idx - i * ncell;
-            const float v = __ldg(phase + (long long)(first_real + i) * nout + (long long)ci * g.Wo + c_lo + c);
+            const long long cell = (long long)ci * g.Wo + c_lo + c;
+            float v = __ldg(phase + (long long)(first_real + i) * nout + cell);
+            // re-referenced to date shift_date when asked (its phase subtracted)
+            if (shift_date >= 0) v -= __ldg(phase + (long long)shift_date * nout + cell);
             float s, cs;
             sincosf(v, &s, &cs);  // NaN phase -> NaN phasor -> pixel marked bad
             ph[idx] = make_float2(cs, s);
@@ -76,7 +81,7 @@ __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constan
 }
 
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
-                            float2 *kappa, cudaStream_t s) {
+                            float2 *kappa, cudaStream_t s, int shift_date) {
     const long long npix = (long long)g.H * g.W;
     if (npix == 0) return cudaSuccess;
     if (g.Ho == 0 || g.Wo == 0) return cudaMemsetAsync(kappa, 0, npix * sizeof(float2), s);
@@ -88,7 +93,8 @@ cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &
     }
     const long long nblocks = (long long)g.Ho * nchunk;
     const long long grid = std::min<long long>(nblocks, (long long)device_sm_count() * 64);
-    k_compress<<<(unsigned)grid, kCompressCols, smem, s>>>(z, n, first_real, g, phase, kappa, nchunk);
+    k_compress<<<(unsigned)grid, kCompressCols, smem, s>>>(z, n, first_real, g, phase, kappa, nchunk,
+                                                             shift_date);
     return cudaGetLastError();
 }
 

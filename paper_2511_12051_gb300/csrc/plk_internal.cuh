@@ -78,8 +78,9 @@ struct StackSource {
 cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
                               float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s,
                               Prof *prof = nullptr, const StackSource *src = nullptr, const Schedule *sch = nullptr);
+// shift_date >= 0: the phases are re-referenced to that date (its phase subtracted).
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
-                            float2 *kappa, cudaStream_t s);
+                            float2 *kappa, cudaStream_t s, int shift_date = -1);
 
 int device_sm_count();
 // Nonzero if a bounded device-side wait gave up since the last call (then cleared).

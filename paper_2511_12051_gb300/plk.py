@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_float), ("mu", ctypes.c_float),
                 ("tol", ctypes.c_float), ("max_iter", ctypes.c_int32), ("cond_max", ctypes.c_float),
                 ("fp64_resolve", ctypes.c_int32), ("err_max", ctypes.c_float), ("cov_precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("ref_scheme", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class StackDesc(ctypes.Structure):
@@ -52,6 +52,8 @@ class StackDesc(ctypes.Structure):
 
 COV_FP32 = 0  # PLK_COV_FP32
 COV_BF16 = 1  # PLK_COV_BF16
+REF_FIRST = 0  # PLK_REF_FIRST
+REF_LAST_REAL = 1  # PLK_REF_LAST_REAL
 
 
 _lock = threading.Lock()

@@ -264,3 +264,47 @@ def test_edge_cases(plk, ctx):
         plk.State(ctx, 10, 10, (5, 11, 1, 1), K_max=20, M_max=15)
     with pytest.raises(plk.PlkError):
         ctx.phase_link(torch.zeros((4, 3), dtype=torch.complex64, device="cuda"), 2, 5)
+
+
+@pytest.mark.parametrize("case", ["cfg1", "cfg3"])
+def test_ministack_step_parity_last_real_scheme(plk, ctx, case, tmp_path):
+    """The production reference scheme (each compressed SLC carries its
+    mini-stack's last real date): every step from identical inputs against the
+    oracle chain in the same scheme."""
+    z, window, M, K_max, nd = chain_case(case)
+    H, W = z.shape[1:]
+    orc = oracle.OracleChain(H, W, window, K_max=K_max, alpha=1e-3, kappa_dtype=np.complex64, scheme="last")
+    prm = plk.default_params(ref_scheme=plk.REF_LAST_REAL)
+    zg = z.cuda()
+    for k, sl in enumerate(synth.ministack_slices(nd, M)):
+        path = str(tmp_path / f"s{k}.plk")
+        write_state_file(path, orc)
+        st = plk.State.load(ctx, path, M_max=M)
+        g = st.step(zg[sl].contiguous(), prm)
+        o = orc.step(z[sl].numpy())
+        live = o["status"] != 3
+        clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+        rep = phase_report(to_np(g["phase"]), o["phase"][o["K_used"]:], clear)
+        assert rep["max"] <= PHASE_TOL, (k, rep)
+        kg = to_np(st.kappa(st.info()["K_used"] - 1))
+        scale = np.abs(z[sl].numpy()).sum(0)
+        assert np.max(np.abs(kg - orc.ring[-1]) / (scale + 1e-6)) < 1e-4
+        st.close()
+
+
+def test_last_real_scheme_noise_free_short_baselines(plk, ctx):
+    n_dates, M, H, W = 20, 5, 24, 48
+    rng = np.random.default_rng(3)
+    t = np.arange(n_dates)
+    phi = 0.3 * t + 0.4 * np.sin(t)
+    amp = rng.rayleigh(1.0, (H, W)) + 0.2
+    psi = rng.uniform(-np.pi, np.pi, (H, W))
+    z = torch.from_numpy((amp[None] * np.exp(1j * (phi[:, None, None] + psi[None]))).astype(np.complex64)).cuda()
+    st = plk.State(ctx, H, W, (3, 5, 1, 1), K_max=3, M_max=M)
+    prm = plk.default_params(ref_scheme=plk.REF_LAST_REAL)
+    for s, sl in enumerate(synth.ministack_slices(n_dates, M)):
+        g = st.step(z[sl].contiguous(), prm)
+        ref_date = 0 if s == 0 else sl.start - 1
+        want = (phi[sl] - phi[ref_date])[:, None, None]
+        assert wrapped_diff(to_np(g["phase"]), want).max() < 1e-4, s
+    st.close()

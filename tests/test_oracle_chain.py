@@ -97,3 +97,40 @@ def test_rms_error_decreases_with_looks():
         errs.append(np.mean(e))
     assert all(a > b for a, b in zip(errs, errs[1:])), errs
     assert errs[-1] < 0.25 * errs[0], errs
+
+
+@pytest.mark.parametrize("window", [(3, 5, 1, 1), (5, 11, 3, 6)])
+def test_chain_last_real_scheme_noise_free(window):
+    # Production scheme (Sec. IV; Supplement): each compressed SLC carries the
+    # phase of its mini-stack's last real date, so the outputs of step s are
+    # the short-baseline interferograms to the last date of step s-1 (to day 1
+    # on the first step), exactly on noise-free stacks.
+    n_dates, M, H, W = 20, 5, 18, 36
+    z, phi = noise_free_stack(n_dates, H, W, seed=2)
+    ch = oracle.OracleChain(H, W, window, K_max=3, alpha=1e-3, scheme="last")
+    for s, sl in enumerate(synth.ministack_slices(n_dates, M)):
+        out = ch.step(z[sl])
+        ref_date = 0 if s == 0 else sl.start - 1
+        want = (phi[sl] - phi[ref_date])[:, None, None]
+        np.testing.assert_allclose(wrapped(out["phase_real"] - want), 0, atol=1e-6)
+        assert np.all(out["phase"][out["K_used"] - 1] == 0.0) if out["K_used"] else True
+
+
+def test_chain_last_real_kappa_is_rotated_first_kappa():
+    # The last-real compressed SLC is the always-first one rotated, cell by
+    # cell, by the linked phase of the last real date: kappa_last =
+    # kappa_first * exp(j phase_last(cell)).
+    spec = synth.config_spec(0, N=8, H=24, W=36, seed=5)
+    z = synth.generate(spec).numpy()
+    window = (5, 11, 3, 6)
+    a = oracle.OracleChain(24, 36, window, K_max=2, scheme="first")
+    b = oracle.OracleChain(24, 36, window, K_max=2, scheme="last")
+    oa, ob = a.step(z), b.step(z)
+    np.testing.assert_allclose(oa["phase"], ob["phase"])  # same linking on the first step
+    last = oa["phase"][-1]
+    Ho, Wo = last.shape
+    ci = np.minimum(np.arange(24) // 3, Ho - 1)
+    cj = np.minimum(np.arange(36) // 6, Wo - 1)
+    rot = np.exp(1j * last[ci[:, None], cj[None, :]])
+    ok = np.isfinite(rot)
+    np.testing.assert_allclose(b.ring[-1][ok], (a.ring[-1] * rot)[ok], rtol=1e-12, atol=1e-9)
