@@ -58,6 +58,9 @@ def _load():
             lib.orc_shp_select.argtypes = [P, i32, i32, i32, i32, i32, i32, f32, P, P]
             lib.orc_covariance.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, P, P]
             lib.orc_phase_link.argtypes = [P, i32, i64, i32, f64, P, P, P, P, P, P]
+            lib.orc_amp_dispersion.argtypes = [P, P, i64, i32, P]
+            lib.orc_ps_regrid.argtypes = [P, i32, i32, i32, i32, i32, i32, P, P, i32, i32, f32, P, P, i32]
+            lib.orc_ps_compress.argtypes = [P, i32, i32, i32, i32, P, P, i32, i32, f32, i32, P]
             lib.orc_temporal_coherence.argtypes = [i32, P, P]
             lib.orc_temporal_coherence.restype = f64
             lib.orc_compress.argtypes = [P, i32, i32, i32, i32, i32, i32, P, P]
@@ -179,6 +182,56 @@ def compress(z: np.ndarray, first_real: int, window, phase: np.ndarray) -> np.nd
     kappa = np.zeros((H, W), np.complex128)
     _load().orc_compress(_ptr(z), N, int(first_real), H, W, sy, sx, _ptr(ph), _ptr(kappa))
     return kappa
+
+
+# Status code of an output cell that takes a PS phase (the phase-linking codes
+# are 0-4: EMI, EMI re-solved in double precision, EVD, no data, not converged).
+PS_STATUS = 5
+
+
+def amp_dispersion(sum_pow: np.ndarray, sum_amp: np.ndarray, n: int) -> np.ndarray:
+    """D_A = sigma_A / mu_A per pixel from the merged sums (single precision; NaN where mu <= 0)."""
+    sp = np.ascontiguousarray(sum_pow, dtype=np.float32)
+    sa = np.ascontiguousarray(sum_amp, dtype=np.float32)
+    assert sp.shape == sa.shape
+    da = np.empty(sp.shape, np.float32)
+    _load().orc_amp_dispersion(_ptr(sp), _ptr(sa), sp.size, int(n), _ptr(da))
+    return da
+
+
+def ps_regrid(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, sum_amp: np.ndarray, n: int,
+              ref: int, da_max: float, phase: np.ndarray, status: np.ndarray):
+    """PS cells of the output grid take the phase of their lowest-D_A PS.
+
+    phase [N - first_real, Ho, Wo] and status [Ho, Wo] are copied and returned
+    updated (float64, uint8)."""
+    wy, wx, sy, sx = window
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    N, H, W = z.shape
+    Ho, Wo = H // sy, W // sx
+    ph = np.array(phase, dtype=np.float64, order="C", copy=True)
+    st = np.array(status, dtype=np.uint8, order="C", copy=True)
+    assert ph.shape == (N - first_real, Ho, Wo) and st.shape == (Ho, Wo)
+    sp = np.ascontiguousarray(sum_pow, dtype=np.float32)
+    sa = np.ascontiguousarray(sum_amp, dtype=np.float32)
+    assert sp.shape == (H, W) and sa.shape == (H, W)
+    _load().orc_ps_regrid(_ptr(z), N, int(first_real), H, W, sy, sx, _ptr(sp), _ptr(sa), int(n), int(ref),
+                          np.float32(da_max), _ptr(ph), _ptr(st), PS_STATUS)
+    return ph, st
+
+
+def ps_compress(z: np.ndarray, first_real: int, sum_pow: np.ndarray, sum_amp: np.ndarray, n: int, ref: int,
+                da_max: float, kappa: np.ndarray, shift: int = -1) -> np.ndarray:
+    """Compressed SLC with every PS pixel compressed on its own phases (a copy of kappa)."""
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    N, H, W = z.shape
+    k = np.array(kappa, dtype=np.complex128, order="C", copy=True)
+    assert k.shape == (H, W)
+    sp = np.ascontiguousarray(sum_pow, dtype=np.float32)
+    sa = np.ascontiguousarray(sum_amp, dtype=np.float32)
+    _load().orc_ps_compress(_ptr(z), N, int(first_real), H, W, _ptr(sp), _ptr(sa), int(n), int(ref),
+                            np.float32(da_max), int(shift), _ptr(k))
+    return k
 
 
 from .chain import OracleChain, ministack  # noqa: E402,F401

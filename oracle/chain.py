@@ -12,7 +12,12 @@ Each step, for new real SLCs z_1..z_M:
   5. EMI phase linking with reference r = the newest compressed SLC, or the
      first real SLC when there is none (Sec. II-B items 1-3), and gamma_t;
   6. compress the real SLCs onto the linked phases (kappa = zeta^H z) and push
-     kappa into the ring.
+     kappa into the ring;
+  7. with a PS threshold (Sec. IV; Supplement, "Regridding PS and DS"), output
+     cells whose decimation block holds a PS take the phases of the one with
+     the lowest amplitude dispersion, relative to the reference entry, and in
+     step 6 each PS pixel is compressed on its own phases (PS are processed at
+     full resolution), so kappa carries the PS's phase at the datum.
 The phases returned for the real dates are relative to the first date of the
 archive, because every kappa inherits the reference phase of the one before.
 
@@ -26,12 +31,14 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import amp_stats, compress, covariance, glrt_threshold, ntri, phase_link, shp_select
+from . import amp_stats, compress, covariance, glrt_threshold, ntri, phase_link, ps_compress, ps_regrid, shp_select
 
 
 def ministack(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, n_eff: int,
-              alpha: float, ref: int, beta: float = 0.0, cond: bool = False, scheme: str = "first") -> dict:
-    """One mini-stack through S2-S7 with statistics already merged."""
+              alpha: float, ref: int, beta: float = 0.0, cond: bool = False, scheme: str = "first",
+              sum_amp: np.ndarray | None = None, ps_da_max: float = 0.0) -> dict:
+    """One mini-stack through S2-S7 with statistics already merged (PS
+    regridding of the returned phases when ps_da_max > 0)."""
     N = z.shape[0]
     c = glrt_threshold(alpha, n_eff)
     mask, count = shp_select(sum_pow, window, np.float32(c))
@@ -41,7 +48,16 @@ def ministack(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, n_eff
     if scheme == "last":
         ph = ph - ph[N - 1][None]  # re-referenced to the last real SLC
     kappa = compress(z, first_real, window, ph)
+    if ps_da_max > 0:
+        assert sum_amp is not None
+        kappa = ps_compress(z, first_real, sum_pow, sum_amp, n_eff, ref, ps_da_max, kappa,
+                            shift=N - 1 if scheme == "last" else -1)
     out.update(mask=mask, count=count, C=C, kappa=kappa, c=c)
+    if ps_da_max > 0:
+        real, st = ps_regrid(z, first_real, window, sum_pow, sum_amp, n_eff, ref, ps_da_max,
+                             out["phase"][first_real:], out["status"])
+        out["phase"] = np.concatenate([out["phase"][:first_real], real], axis=0)
+        out["status"] = st
     return out
 
 
@@ -49,9 +65,10 @@ class OracleChain:
     """Sequential processing state: kappa ring, merged power sums, image count."""
 
     def __init__(self, H: int, W: int, window, K_max: int, alpha: float = 1e-3, beta: float = 0.0,
-                 kappa_dtype=np.complex128, scheme: str = "first"):
+                 kappa_dtype=np.complex128, scheme: str = "first", ps_da_max: float = 0.0):
         assert scheme in ("first", "last")
         self.scheme = scheme
+        self.ps_da_max = ps_da_max
         # kappa_dtype=np.complex64 stores each compressed SLC rounded to the
         # single-precision complex samples a stored SLC has (the form the GPU
         # state keeps), so both sides can start a step from identical inputs.
@@ -75,7 +92,8 @@ class OracleChain:
         parts.append(new_slc.astype(np.complex128))
         z = np.concatenate(parts, axis=0)
         ref = K - 1 if K > 0 else 0
-        out = ministack(z, K, self.window, self.sum_pow, self.n, self.alpha, ref, self.beta, cond, self.scheme)
+        out = ministack(z, K, self.window, self.sum_pow, self.n, self.alpha, ref, self.beta, cond, self.scheme,
+                        self.sum_amp, self.ps_da_max)
         self.ring.append(out["kappa"].astype(self.kappa_dtype).astype(np.complex128))
         if len(self.ring) > self.K_max:
             self.ring.pop(0)

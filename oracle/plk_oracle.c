@@ -17,9 +17,13 @@
  *                    Sec. II-A reference phase
  *   temporal_coh     Sec. III-C, eq. (temporal-coherence)
  *   compress         Sec. II-B, compressed SLC kappa = zeta^H z
+ *   amp_dispersion   Sec. III-A, D_A = sigma_A / mu_A
+ *   ps_regrid        Sec. IV (PS threshold on D_A) and the Supplement's
+ *                    regridding of PS and DS onto the output grid
  *
- * Two quantities decide integers (the SHP mask bits): the per-pixel power sums
- * and the threshold comparison.  The paper fixes no precision for them, so they
+ * Three quantities decide integers (the SHP mask bits and the PS flags): the per-pixel power sums
+ * the threshold comparison and the amplitude dispersion.  The paper fixes no
+ * precision for them, so they
  * are taken in single precision with one fixed operation order (no fused
  * multiply-add; build with -ffp-contract=off), the precision of the GPU kernel.
  * Everything else is IEEE double.
@@ -523,4 +527,117 @@ void orc_compress(const double *z, int N, int first_real, int H, int W, int sy, 
             }
             kc[q] = bad ? 0.0 : k;
         }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Amplitude dispersion (Sec. III-A): D_A = sigma_A / mu_A, the mean and     */
+/* standard deviation of the pixel amplitude over the images seen so far.   */
+/* With one weight per image, eqs. (merged-mean) and (merged-variance) give */
+/* them from the running sums SA = sum A and SP = sum A^2 = sum |z|^2:      */
+/*   mu = SA / n,  sigma^2 = SP / n - mu^2  (population variance, >= 0).    */
+/* Single precision, each operation rounded as written.  mu <= 0 (a pixel   */
+/* that was always zero) has no dispersion: NaN.                            */
+/* ------------------------------------------------------------------------ */
+static float amp_dispersion_one(float sp, float sa, int n)
+{
+    const float nf = (float)n;
+    const float mu = sa / nf;
+    if (!(mu > 0.0f)) return NAN;
+    const float e2 = sp / nf;
+    const float mu2 = mu * mu;
+    float var = e2 - mu2;
+    if (var < 0.0f) var = 0.0f;
+    return sqrtf(var) / mu;
+}
+
+void orc_amp_dispersion(const float *sum_pow, const float *sum_amp, long npix, int n, float *da)
+{
+    for (long q = 0; q < npix; ++q) da[q] = amp_dispersion_one(sum_pow[q], sum_amp[q], n);
+}
+
+/* ------------------------------------------------------------------------ */
+/* PS selection and regridding (Sec. IV: a pixel is a PS when D_A <= the    */
+/* threshold, 0.2 in production, at full resolution; Supplement,            */
+/* "Regridding PS and DS to 30 m resolution").  Each output cell covers the  */
+/* sy x sx full-resolution pixels of its decimation block (the last cell    */
+/* row/column also the rows/columns beyond the grid, as for compress):      */
+/*   no PS in the block    -> the cell keeps its phase-linking phases;      */
+/*   one PS                -> that PS's single-reference phases;            */
+/*   several PS            -> those of the PS with the lowest D_A (the      */
+/*                            first in row-major order on a tie).           */
+/* The single-reference phase of date i at PS q is arg(z_i(q) conj z_r(q)),  */
+/* r the mini-stack's reference entry, so it shares the DS phases' datum.   */
+/* Those phases must be defined: a pixel with a zero sample at r or on a    */
+/* real date is not taken.  phase [N-first_real][Ho][Wo] (double) and       */
+/* status [Ho][Wo] are updated in place; PS cells get status ps_code.       */
+/* ------------------------------------------------------------------------ */
+static int ps_phases_defined(const cplx *zc, int N, int first_real, long npix, int ref, long q)
+{
+    if (zc[(long)ref * npix + q] == 0.0) return 0;
+    for (int i = first_real; i < N; ++i)
+        if (zc[(long)i * npix + q] == 0.0) return 0;
+    return 1;
+}
+
+void orc_ps_regrid(const double *z, int N, int first_real, int H, int W, int sy, int sx,
+                   const float *sum_pow, const float *sum_amp, int n, int ref, float da_max,
+                   double *phase, uint8_t *status, int ps_code)
+{
+    const int Ho = H / sy, Wo = W / sx;
+    const long npix = (long)H * W, nout = (long)Ho * Wo;
+    const cplx *zc = (const cplx *)z;
+    for (int ci = 0; ci < Ho; ++ci)
+        for (int cj = 0; cj < Wo; ++cj) {
+            const int y1 = (ci == Ho - 1) ? H : (ci + 1) * sy;
+            const int x1 = (cj == Wo - 1) ? W : (cj + 1) * sx;
+            long best_q = -1;
+            float best = 0.0f;
+            for (int y = ci * sy; y < y1; ++y)
+                for (int x = cj * sx; x < x1; ++x) {
+                    const long q = (long)y * W + x;
+                    const float da = amp_dispersion_one(sum_pow[q], sum_amp[q], n);
+                    if (isnan(da) || !(da <= da_max)) continue;       /* not a PS */
+                    if (!ps_phases_defined(zc, N, first_real, npix, ref, q)) continue;
+                    if (best_q < 0 || da < best) {
+                        best_q = q;
+                        best = da;
+                    }
+                }
+            if (best_q < 0) continue;
+            const long o = (long)ci * Wo + cj;
+            const cplx r = zc[(long)ref * npix + best_q];
+            for (int i = first_real; i < N; ++i)
+                phase[(long)(i - first_real) * nout + o] = carg(zc[(long)i * npix + best_q] * conj(r));
+            status[o] = (uint8_t)ps_code;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compressed SLC at the PS pixels (Sec. II-B, kappa = zeta^H z, with the   */
+/* PS processed at full resolution, Sec. IV): a PS pixel (same test as in   */
+/* orc_ps_regrid, every PS of a block, not only the selected one) is        */
+/* compressed on its own single-reference phases theta_i = arg(z_i conj     */
+/* z_ref), re-referenced to date shift (theta_i - theta_shift) when         */
+/* shift >= 0:  kappa(q) = sum_{i >= first_real} exp(-j theta_i) z_i(q).    */
+/* kappa [H][W] is overwritten at those pixels only.                         */
+/* ------------------------------------------------------------------------ */
+void orc_ps_compress(const double *z, int N, int first_real, int H, int W, const float *sum_pow,
+                     const float *sum_amp, int n, int ref, float da_max, int shift, double *kappa)
+{
+    const long npix = (long)H * W;
+    const cplx *zc = (const cplx *)z;
+    cplx *kc = (cplx *)kappa;
+    for (long q = 0; q < npix; ++q) {
+        const float da = amp_dispersion_one(sum_pow[q], sum_amp[q], n);
+        if (isnan(da) || !(da <= da_max)) continue;
+        if (!ps_phases_defined(zc, N, first_real, npix, ref, q)) continue;
+        const cplx r = zc[(long)ref * npix + q];
+        const double th_s = shift >= 0 ? carg(zc[(long)shift * npix + q] * conj(r)) : 0.0;
+        cplx k = 0.0;
+        for (int i = first_real; i < N; ++i) {
+            const double th = carg(zc[(long)i * npix + q] * conj(r)) - th_s;
+            k += cexp(-I * th) * zc[(long)i * npix + q];
+        }
+        kc[q] = k;
+    }
 }
