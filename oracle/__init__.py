@@ -190,7 +190,8 @@ PS_STATUS = 5
 
 
 def amp_dispersion(sum_pow: np.ndarray, sum_amp: np.ndarray, n: int) -> np.ndarray:
-    """D_A = sigma_A / mu_A per pixel from the merged sums (single precision; NaN where mu <= 0)."""
+    """D_A = sigma_A / mu_A = sqrt(n SP - SA^2) / SA per pixel from the merged sums (single precision;
+    NaN where SA <= 0)."""
     sp = np.ascontiguousarray(sum_pow, dtype=np.float32)
     sa = np.ascontiguousarray(sum_amp, dtype=np.float32)
     assert sp.shape == sa.shape

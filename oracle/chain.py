@@ -48,7 +48,8 @@ def ministack(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, n_eff
     if scheme == "last":
         ph = ph - ph[N - 1][None]  # re-referenced to the last real SLC
     kappa = compress(z, first_real, window, ph)
-    if ps_da_max > 0:
+    has_cells = C.shape[0] * C.shape[1] > 0  # no output grid: nothing is linked, kappa stays 0
+    if ps_da_max > 0 and has_cells:
         assert sum_amp is not None
         kappa = ps_compress(z, first_real, sum_pow, sum_amp, n_eff, ref, ps_da_max, kappa,
                             shift=N - 1 if scheme == "last" else -1)

@@ -534,20 +534,20 @@ void orc_compress(const double *z, int N, int first_real, int H, int W, int sy, 
 /* standard deviation of the pixel amplitude over the images seen so far.   */
 /* With one weight per image, eqs. (merged-mean) and (merged-variance) give */
 /* them from the running sums SA = sum A and SP = sum A^2 = sum |z|^2:      */
-/*   mu = SA / n,  sigma^2 = SP / n - mu^2  (population variance, >= 0).    */
-/* Single precision, each operation rounded as written.  mu <= 0 (a pixel   */
-/* that was always zero) has no dispersion: NaN.                            */
+/*   mu = SA / n,  sigma^2 = SP / n - mu^2  (population variance, >= 0),    */
+/* so that D_A = sqrt(n SP - SA^2) / SA.  That last form is the one taken:  */
+/* single precision, each operation rounded as written, the difference     */
+/* clamped at 0.  SA <= 0 (a pixel that was always zero) has no dispersion: */
+/* NaN.                                                                     */
 /* ------------------------------------------------------------------------ */
 static float amp_dispersion_one(float sp, float sa, int n)
 {
-    const float nf = (float)n;
-    const float mu = sa / nf;
-    if (!(mu > 0.0f)) return NAN;
-    const float e2 = sp / nf;
-    const float mu2 = mu * mu;
-    float var = e2 - mu2;
-    if (var < 0.0f) var = 0.0f;
-    return sqrtf(var) / mu;
+    if (!(sa > 0.0f)) return NAN;
+    const float nsp = (float)n * sp;
+    const float sa2 = sa * sa;
+    float d = nsp - sa2;
+    if (d < 0.0f) d = 0.0f;
+    return sqrtf(d) / sa;
 }
 
 void orc_amp_dispersion(const float *sum_pow, const float *sum_amp, long npix, int n, float *da)

@@ -255,3 +255,18 @@ def test_chain_ps_keeps_its_datum(scheme):
         ref_date = 0 if (s == 0 or scheme == "first") else sl.start - 1
         want = np.angle(np.exp(1j * (phi_ps[sl] - phi_ps[ref_date])))
         np.testing.assert_allclose(np.angle(np.exp(1j * (out["phase_real"][:, 1, 1] - want))), 0, atol=1e-5)
+
+
+def test_regrid_lowest_da_without_reference_sample_gives_way():
+    # The lowest-D_A pixel of the block has a zero reference sample (a
+    # compressed SLC that was zero there): the next lowest is taken.
+    N, win = 9, (3, 5, 3, 6)
+    z = background(N, 3, 6, 11)
+    t = np.arange(1, N)
+    plant(z[1:], 0, 4, 2.0, 0.1 * t)                       # D_A = 0, but ...
+    z[0, 0, 4] = 0                                         # ... no reference sample
+    plant(z[1:], 2, 1, [1.0, 1.2] * 4, -0.2 * t)           # D_A = 1/11
+    z[0, 2, 1] = np.complex64(1.0)
+    ph, st = regrid(z, win, 0.2, first_real=1, ref=0)
+    assert st[0, 0] == oracle.PS_STATUS
+    np.testing.assert_allclose(ph[:, 0, 0], np.angle(np.exp(-0.2j * t)), atol=1e-6, rtol=0)
