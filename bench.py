@@ -30,6 +30,7 @@ METRIC = "phase-linked pixels/s (N=15, 11×5 window) and % of HBM/FP32 roofline"
 UNIT = "output px/s"
 WINDOW = (5, 11, 3, 6)  # wy, wx, sy, sx  ("11 x 5", strides 6 x 3)
 N_DATES = 15
+PS_DA_MAX = 0.2  # production PS threshold on the amplitude dispersion (Sec. IV)
 H_FULL, W_FULL = 4096, 16384
 WORKLOAD = "burst-shaped mini-stack: N=15 complex64 SLCs x 4096x16384 px, 11x5 window, output strides 6x3"
 
@@ -347,7 +348,10 @@ def main():
     ap.add_argument("--cols", type=int, default=W_FULL, help="image columns (smaller cases for profiling only)")
     ap.add_argument("--cov-precision", default="fp32", choices=["fp32", "bf16"],
                     help="coherence arithmetic of the timed step (fp32: the plain path)")
-    ap.add_argument("--no-modes", action="store_true", help="skip timing the bfloat16-coherence mode beside it")
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip timing the bfloat16-coherence and PS-regridding modes beside it")
+    ap.add_argument("--ps-da-max", type=float, default=0.0,
+                    help="PS threshold on the amplitude dispersion in the timed step (0: no PS regridding)")
     ap.add_argument("--workload", default="burst", choices=["burst", "batch", "adjoint"],
                     help="burst: the headline mini-stack step; batch: 64 uneven stacks in one recorded graph; "
                          "adjoint: forward and backward of the phase linking on N=20 x 1024x1024")
@@ -383,7 +387,7 @@ def main():
     ctx = plk.Context(dev, stream)
     st = plk.State(ctx, spec.H, spec.W, WINDOW, K_max=6, M_max=N_DATES)
     prec = plk.COV_BF16 if args.cov_precision == "bf16" else plk.COV_FP32
-    params = plk.default_params(cov_precision=prec)
+    params = plk.default_params(cov_precision=prec, ps_da_max=args.ps_da_max)
     with torch.cuda.stream(stream):
         out = st.step(z, params)  # allocates the output tensors once
     torch.cuda.synchronize(dev)
@@ -483,11 +487,8 @@ def main():
                "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_e2e / ne}
         del zh, oh
 
-    # ------------------------------------- bfloat16-coherence mode beside it
-    modes = None
-    if not args.no_modes and prec == plk.COV_FP32:
-        alt = plk.default_params(cov_precision=plk.COV_BF16)
-
+    # ------------------------- other modes of the same step, timed beside it
+    def time_mode(alt):
         def alt_step():
             st.reset()
             st.step(z, alt, out=out)
@@ -509,10 +510,19 @@ def main():
         kalt = ctx.profile_collect()
         ctx.profile(False)
         ms_alt = pdist.max_over_ranks(g0.elapsed_time(g1), dev)
-        modes = {"bf16_covariance": {
-            "value": npx * world * args.steps / (ms_alt / 1e3), "unit": UNIT, "ms_per_step": ms_alt / args.steps,
-            "kernels_ms_per_step": {kk: v[0] / args.steps for kk, v in kalt.items()},
-            "accuracy": "measured against the FP64 oracle by tests/test_gpu_bf16.py (linked-phase p50/p99/max)"}}
+        return {"value": npx * world * args.steps / (ms_alt / 1e3), "unit": UNIT, "ms_per_step": ms_alt / args.steps,
+                "kernels_ms_per_step": {kk: v[0] / args.steps for kk, v in kalt.items()}}
+
+    modes = None
+    if not args.no_modes and prec == plk.COV_FP32 and args.ps_da_max == 0:
+        modes = {}
+        modes["bf16_covariance"] = time_mode(plk.default_params(cov_precision=plk.COV_BF16))
+        modes["bf16_covariance"]["accuracy"] = ("measured against the FP64 oracle by tests/test_gpu_bf16.py "
+                                                "(linked-phase p50/p99/max)")
+        modes["ps_regrid"] = time_mode(plk.default_params(ps_da_max=PS_DA_MAX))
+        modes["ps_regrid"]["ps_da_max"] = PS_DA_MAX
+        modes["ps_regrid"]["ps_cells"] = int((out["status"] == plk.PX_PS).sum().item())
+        modes["ps_regrid"]["output_cells"] = npx
 
     # ---------------------------------------------------------- CPU baseline
     cpu = None
@@ -543,6 +553,7 @@ def main():
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kernels.items()},
             "pixel_status_hist": status_hist,
             "cov_precision": args.cov_precision,
+            "ps_da_max": args.ps_da_max,
             "modes": modes,
         }
         print(json.dumps(line), flush=True)

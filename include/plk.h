@@ -55,7 +55,9 @@ enum {
     PLK_PX_EMI_FP64 = 1,  /* EMI solution re-solved in double precision */
     PLK_PX_EVD = 2,       /* inversion of |C| failed: EVD fallback (Sec. III-B) */
     PLK_PX_NODATA = 3,    /* zero-power centre / empty neighbourhood: NaN outputs */
-    PLK_PX_NOCONV = 4     /* inverse iteration hit max_iter; last iterate kept */
+    PLK_PX_NOCONV = 4,    /* inverse iteration hit max_iter; last iterate kept */
+    PLK_PX_PS = 5         /* output cell takes the phase of a persistent scatterer
+                             (plk_ps_regrid, Supplement "Regridding PS and DS") */
 };
 
 typedef struct plk_c64 { float re, im; } plk_c64;
@@ -87,7 +89,14 @@ typedef struct plk_params {
                               single precision on the tensor cores; N <= 32) */
     int32_t ref_scheme;    /* mini-stack reference scheme of plk_ministack_step:
                               PLK_REF_FIRST (default) or PLK_REF_LAST_REAL */
-    int32_t reserved[1];
+    float ps_da_max;       /* plk_ministack_step: when > 0, output cells whose
+                              decimation block holds a pixel with amplitude
+                              dispersion D_A <= ps_da_max take that persistent
+                              scatterer's phase (plk_ps_regrid), and every PS
+                              pixel is compressed on its own phases
+                              arg(z_i conj z_ref), so that later mini-stacks keep
+                              its datum; default 0 (off); the paper's production
+                              value is 0.2 */
 } plk_params;
 
 /* Mini-stack reference schemes (plk_params.ref_scheme).  Both link each
@@ -252,11 +261,36 @@ plk_status plk_state_load(plk_ctx *ctx, const char *path, int M_max, plk_state *
  * phase [M][Ho][Wo] relative to the first date of the archive (PLK_REF_FIRST)
  * or to the previous mini-stack's last real date (PLK_REF_LAST_REAL; the
  * first date on the first step), tcoh [Ho][Wo],
- * status [Ho][Wo]; shp_count [Ho][Wo] may be NULL.  1 <= M <= M_max and
- * M + (compressed SLCs held) >= 2.  params NULL = defaults. */
+ * status [Ho][Wo]; shp_count [Ho][Wo] may be NULL.  With params->ps_da_max > 0
+ * the output cells holding a persistent scatterer take its phases (status
+ * PLK_PX_PS, tcoh unchanged; plk_ps_regrid) and each PS pixel's kappa is formed
+ * on its own phases.  1 <= M <= M_max and M + (compressed SLCs held) >= 2.
+ * params NULL = defaults. */
 plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
                               const plk_params *params, float *phase, float *tcoh,
                               uint8_t *status, uint16_t *shp_count);
+
+/* ------------------------------------------ persistent scatterers */
+
+/* PS selection and regridding (Sec. III-A, eq. (amplitude dispersion); Sec. IV;
+ * Supplement "Regridding PS and DS to 30 m resolution").  Per full-resolution
+ * pixel, D_A = sigma_A / mu_A from the merged sums, with mu = sum_amp / n_eff
+ * and the population deviation sigma, taken as
+ * D_A = sqrt(max(n_eff * sum_pow - sum_amp^2, 0)) / sum_amp in single
+ * precision in this order with correctly rounded operations and no fused
+ * multiply-add; a pixel with sum_amp > 0,
+ * D_A <= da_max and nonzero samples at ref_idx and on every real date (so
+ * that its phases are defined) is a PS.  Per output cell (its sy x sx decimation block; the
+ * last row/column of cells also takes the rows/columns beyond the grid): with
+ * no PS the phases are left as they are (the DS phase-linking result); else
+ * the PS with the lowest D_A (the first in row-major order on a tie) gives
+ * phase[j][cell] = arg(z_{first_real+j}(q) conj(z_ref(q))) for every real date
+ * j, and status[cell] = PLK_PX_PS.  slc [N][H][W] (the mini-stack, reference
+ * entry ref_idx); sum_pow, sum_amp [H][W]; phase [N-first_real][Ho][Wo] and
+ * status [Ho][Wo] are updated in place.  Errors: EINVAL, ECUDA. */
+plk_status plk_ps_regrid(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real, int H, int W, plk_window win,
+                         const float *sum_pow, const float *sum_amp, int n_eff, int ref_idx, float da_max,
+                         float *phase, uint8_t *status);
 
 /* ----------------------------------------------------------- adjoint */
 

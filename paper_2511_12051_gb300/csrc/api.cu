@@ -19,6 +19,8 @@ struct plk_state {
     float2 **ring;       // K_max planes [H][W]
     float *sum_pow;      // [H][W]
     float *sum_amp;      // [H][W]
+    float *da;           // [H][W] amplitude dispersion of the last step with PS selection
+    float *amp_new;      // [H][W] that step's sum of |z| over its real SLCs, at its PS pixels
     uint64_t *mask;      // [Ho][Wo][nwords]
     uint16_t *count;     // [Ho][Wo]
     float2 *C;           // [Ho*Wo][ntri(K_max+M_max)]
@@ -111,7 +113,7 @@ using plk::Geom;
 using plk::Planes;
 
 plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
-                                  int *cov_precision, int *ref_scheme) {
+                                  int *cov_precision, int *ref_scheme, float *ps_da_max) {
     out->work = ctx->work;
     plk_params p;
     if (params) p = *params;
@@ -119,9 +121,11 @@ plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::E
     if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
         !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0) ||
         (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16) ||
-        (p.ref_scheme != PLK_REF_FIRST && p.ref_scheme != PLK_REF_LAST_REAL))
+        (p.ref_scheme != PLK_REF_FIRST && p.ref_scheme != PLK_REF_LAST_REAL) ||
+        !(p.ps_da_max >= 0.f && p.ps_da_max < 1e30f))
         return fail(ctx, PLK_EINVAL, "bad plk_params");
     if (cov_precision) *cov_precision = p.cov_precision;
+    if (ps_da_max) *ps_da_max = p.ps_da_max;
     if (ref_scheme) *ref_scheme = p.ref_scheme;
     out->beta = p.beta;
     out->mu = p.mu;
@@ -402,6 +406,29 @@ plk_status plk_compress(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real,
     return PLK_OK;
 }
 
+plk_status plk_ps_regrid(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real, int H, int W, plk_window win,
+                         const float *sum_pow, const float *sum_amp, int n_eff, int ref_idx, float da_max,
+                         float *phase, uint8_t *status) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_ps_regrid: null ctx");
+    if (N < 1 || N > PLK_MAX_N || first_real < 0 || first_real >= N || ref_idx < 0 || ref_idx >= N || H < 1 ||
+        W < 1 || !window_ok(win) || n_eff < 1 || !(da_max >= 0.f && da_max < 1e30f))
+        return fail(ctx, PLK_EINVAL, "plk_ps_regrid: bad argument");
+    const Geom g = plk::make_geom(H, W, win);
+    if ((long long)g.Ho * g.Wo == 0) return PLK_OK;
+    if (!slc || !sum_pow || !sum_amp || !phase || !status) return fail(ctx, PLK_EINVAL, "plk_ps_regrid: null pointer");
+    if (!aligned(slc, 8) || !aligned(sum_pow, 4) || !aligned(sum_amp, 4) || !aligned(phase, 4))
+        return fail(ctx, PLK_EINVAL, "plk_ps_regrid: misaligned pointer");
+    DeviceGuard dg(ctx->device);
+    Planes z{};
+    for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
+    ctx->prof.begin("ps_regrid", ctx->stream);
+    cudaError_t e = plk::launch_ps_regrid(z, N, first_real, ref_idx, g, sum_pow, sum_amp, n_eff, da_max, phase,
+                                          status, ctx->stream);
+    ctx->prof.end(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ps_regrid");
+    return PLK_OK;
+}
+
 // ----------------------------------------------------------------- adjoint
 
 plk_status plk_backward_workspace_size(int N, int H, int W, plk_window win, size_t *bytes) {
@@ -455,6 +482,8 @@ static void state_free(plk_state *st) {
     }
     cudaFree(st->sum_pow);
     cudaFree(st->sum_amp);
+    cudaFree(st->da);
+    cudaFree(st->amp_new);
     cudaFree(st->mask);
     cudaFree(st->count);
     cudaFree(st->C);
@@ -487,6 +516,8 @@ plk_status plk_state_create(plk_ctx *ctx, int H, int W, plk_window win, int K_ma
     for (int i = 0; ok && i < K_max; ++i) ok = cudaMalloc(&st->ring[i], npix * sizeof(float2)) == cudaSuccess;
     ok = ok && cudaMalloc(&st->sum_pow, npix * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&st->sum_amp, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->da, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&st->amp_new, npix * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&st->mask, (nout > 0 ? nout : 1) * g.nwords * sizeof(uint64_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&st->count, (nout > 0 ? nout : 1) * sizeof(uint16_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&st->C, (nout > 0 ? nout : 1) * plk::ntri(Nmax) * sizeof(float2)) == cudaSuccess;
@@ -633,7 +664,8 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     plk::EmiParams prm;
     double alpha;
     int cov_precision = PLK_COV_FP32, ref_scheme = PLK_REF_FIRST;
-    plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision, &ref_scheme);
+    float ps_da_max = 0.f;
+    plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision, &ref_scheme, &ps_da_max);
     if (ps != PLK_OK) return ps;
     if (cov_precision == PLK_COV_BF16 && st->K_used + M > 32)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: bfloat16 coherence needs N <= 32");
@@ -647,11 +679,18 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     Planes znew{};
     for (int t = 0; t < M; ++t) znew.p[t] = reinterpret_cast<const float2 *>(new_slc) + (long long)t * npix;
     ctx->prof.begin("amp_stats", s);
+    const int n_eff = st->n_eff + M;
+    // With PS selection S1 also writes D_A of the merged sums (+inf where a new
+    // sample is zero) and, at PS pixels, the amplitude sum of the new images.
+    plk::PsStats pst;
+    pst.da = st->da;
+    pst.amp_new = st->amp_new;
+    pst.n_eff = (float)n_eff;
+    pst.da_max = ps_da_max;
     cudaError_t e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(new_slc), M, npix, st->sum_pow,
-                                          st->sum_amp, st->n_eff > 0 ? 1 : 0, s);
+                                          st->sum_amp, st->n_eff > 0 ? 1 : 0, s, ps_da_max > 0.f ? &pst : nullptr);
     ctx->prof.end(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: amp_stats");
-    const int n_eff = st->n_eff + M;
 
     // S2: SHP masks on the merged statistics.
     double c;
@@ -683,6 +722,14 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
                             cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: phase copy");
     }
+    // PS cells of the output take their PS's phases; below, each PS pixel is
+    // compressed on its own phases, every other pixel on its cell's linked phases.
+    if (ps_da_max > 0.f && nout > 0) {
+        ctx->prof.begin("ps_regrid", s);
+        e = plk::launch_ps_regrid(z, N, K, ref, g, nullptr, nullptr, n_eff, ps_da_max, phase, status, s, st->da);
+        ctx->prof.end(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: ps_regrid");
+    }
 
     // S7-S8: compress the real SLCs and push kappa into the ring.
     if (st->K_max > 0) {
@@ -691,8 +738,15 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
         else slot = st->head;
         ctx->prof.begin("compress", s);
         // PLK_REF_LAST_REAL: the new compressed SLC carries the last real date's phase.
+        plk::PsSelect psel;
+        if (ps_da_max > 0.f && nout > 0) {
+            psel.da = st->da;
+            psel.amp_new = st->amp_new;
+            psel.da_max = ps_da_max;
+            psel.ref = ref;
+        }
         e = plk::launch_compress(z, N, K, g, st->phase_all, st->ring[slot], s,
-                                 ref_scheme == PLK_REF_LAST_REAL ? N - 1 : -1);
+                                 ref_scheme == PLK_REF_LAST_REAL ? N - 1 : -1, psel);
         ctx->prof.end(s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: compress");
         if (K < st->K_max) st->K_used = K + 1;

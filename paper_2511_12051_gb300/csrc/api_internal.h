@@ -31,7 +31,7 @@ bool window_ok(plk_window w);
 inline bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 // plk_params (NULL = defaults) -> kernel parameters, GLRT size and coherence precision.
 plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
-                          int *cov_precision = nullptr, int *ref_scheme = nullptr);
+                          int *cov_precision = nullptr, int *ref_scheme = nullptr, float *ps_da_max = nullptr);
 
 // Make a device current for the duration of a call.
 struct DeviceGuard {

@@ -9,9 +9,16 @@
 // the cells its columns fall in into unit phasors exp(-j phi) in shared memory
 // (one sincosf per cell and date, not per pixel), then streams the pixels:
 // one thread per column, eight dates in flight per thread.  HBM-streaming.
+//
+// With PS selection on, a persistent scatterer is compressed on its own
+// phases theta_i = arg(z_i conj z_ref) (minus theta at shift_date when
+// re-referenced) instead of its cell's: then every term conj(zeta_i) z_i is
+// |z_i| times the unit phasor u of z_ref (of z at shift_date), so
+// kappa = (sum_i |z_i|) u, and the next mini-stack's PS phases keep the datum.
+// The amplitude sum over the real dates is the one S1 took for them.
 #include <algorithm>
 
-#include "plk_internal.cuh"
+#include "ps.cuh"
 
 namespace plk {
 
@@ -20,10 +27,11 @@ constexpr int kCompressCols = 256;
 // Cells one block's columns can touch: 256 / sx + 2 at most.
 static int max_cells(int sx) { return kCompressCols / sx + 2; }
 
+template <bool PS>
 __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constant__ Planes z, int n, int first_real,
                                                            const Geom g, const float *__restrict__ phase,
                                                            float2 *__restrict__ kappa, int nchunk,
-                                                           int shift_date) {
+                                                           int shift_date, const PsSelect ps) {
     extern __shared__ float2 ph[];  // (n - first_real) x ncell phasors, date-major
     const long long nout = (long long)g.Ho * g.Wo;
     const int nr = n - first_real;
@@ -53,6 +61,7 @@ __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constan
         for (int y = y_lo; y < y_hi; ++y) {
             const long long q = (long long)y * g.W + x;
             float kr = 0.f, ki = 0.f;
+            float2 last = make_float2(0.f, 0.f);  // PS: the last real date's sample
             bool bad = false;
             int i = 0;
             for (; i + 8 <= nr; i += 8) {
@@ -67,6 +76,7 @@ __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constan
                     kr += e.x * v[u].x + e.y * v[u].y;
                     ki += e.x * v[u].y - e.y * v[u].x;
                 }
+                if (PS) last = v[7];
             }
             for (; i < nr; ++i) {
                 const float2 e = ph[i * ncell + c];
@@ -74,6 +84,14 @@ __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constan
                 bad |= isnan(e.x);
                 kr += e.x * v.x + e.y * v.y;
                 ki += e.x * v.y - e.y * v.x;
+                if (PS) last = v;
+            }
+            if (PS && __ldg(ps.da + q) <= ps.da_max && ref_sample_nonzero(z, ps.ref, q)) {
+                // a PS: compressed on its own phases, kappa = (sum |z_i|) u
+                const float2 u = shift_date == n - 1 ? last : __ldg(z.p[shift_date >= 0 ? shift_date : ps.ref] + q);
+                const float sc = __ldg(ps.amp_new + q) * rhypotf(u.x, u.y);
+                kappa[q] = make_float2(u.x * sc, u.y * sc);
+                continue;
             }
             kappa[q] = bad ? make_float2(0.f, 0.f) : make_float2(kr, ki);
         }
@@ -81,20 +99,20 @@ __global__ void __launch_bounds__(kCompressCols) k_compress(const __grid_constan
 }
 
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
-                            float2 *kappa, cudaStream_t s, int shift_date) {
+                            float2 *kappa, cudaStream_t s, int shift_date, const PsSelect &ps) {
     const long long npix = (long long)g.H * g.W;
     if (npix == 0) return cudaSuccess;
     if (g.Ho == 0 || g.Wo == 0) return cudaMemsetAsync(kappa, 0, npix * sizeof(float2), s);
     const int nchunk = (g.W + kCompressCols - 1) / kCompressCols;
     const size_t smem = (size_t)std::max(n - first_real, 1) * max_cells(g.sx) * sizeof(float2);
+    auto kern = ps.da != nullptr ? k_compress<true> : k_compress<false>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const long long nblocks = (long long)g.Ho * nchunk;
     const long long grid = std::min<long long>(nblocks, (long long)device_sm_count() * 64);
-    k_compress<<<(unsigned)grid, kCompressCols, smem, s>>>(z, n, first_real, g, phase, kappa, nchunk,
-                                                             shift_date);
+    kern<<<(unsigned)grid, kCompressCols, smem, s>>>(z, n, first_real, g, phase, kappa, nchunk, shift_date, ps);
     return cudaGetLastError();
 }
 

@@ -5,16 +5,27 @@
 // the threshold product decide mask bits, so they use explicitly rounded
 // single-precision operations (__fmul_rn / __fadd_rn, never contracted into
 // an FMA) in one fixed order.
-#include "plk_internal.cuh"
+//
+// With PS outputs, S1 also writes D_A of the merged sums per pixel (Sec.
+// III-A) where it is within the threshold or near it, +inf elsewhere and where
+// one of the new samples is zero, and, at the pixels with D_A <= da_max, this
+// mini-stack's amplitude sum: the PS test of the
+// regridding and compression passes then reads one float per pixel and no
+// samples, and compression reads the amplitude sum at PS pixels only.
+#include <algorithm>
+
+#include "ps.cuh"
 
 namespace plk {
 
-__global__ void __launch_bounds__(256) k_amp_stats(const float2 *__restrict__ z, int n, long long npix,
+template <bool DA>
+__global__ void __launch_bounds__(256, 8) k_amp_stats(const float2 *__restrict__ z, int n, long long npix,
                                                    float *__restrict__ sum_pow, float *__restrict__ sum_amp,
-                                                   int accumulate) {
+                                                   int accumulate, const PsStats ps) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
         float P = 0.0f, A = 0.0f;
+        bool nz = true;  // every new sample nonzero
         int t = 0;
         // Eight dates in flight per thread; the sums still run in date order.
         for (; t + 8 <= n; t += 8) {
@@ -26,6 +37,7 @@ __global__ void __launch_bounds__(256) k_amp_stats(const float2 *__restrict__ z,
                 const float q = __fadd_rn(__fmul_rn(v[u].x, v[u].x), __fmul_rn(v[u].y, v[u].y));
                 P = __fadd_rn(P, q);
                 A = __fadd_rn(A, __fsqrt_rn(q));
+                if (DA) nz &= (v[u].x != 0.f) | (v[u].y != 0.f);
             }
         }
         for (; t < n; ++t) {
@@ -33,13 +45,28 @@ __global__ void __launch_bounds__(256) k_amp_stats(const float2 *__restrict__ z,
             const float q = __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
             P = __fadd_rn(P, q);
             A = __fadd_rn(A, __fsqrt_rn(q));
+            if (DA) nz &= (v.x != 0.f) | (v.y != 0.f);
         }
+        const float A_new = A;
         if (accumulate) {
-            sum_pow[p] = __fadd_rn(sum_pow[p], P);
-            if (sum_amp) sum_amp[p] = __fadd_rn(sum_amp[p], A);
-        } else {
-            sum_pow[p] = P;
-            if (sum_amp) sum_amp[p] = A;
+            P = __fadd_rn(sum_pow[p], P);
+            if (sum_amp) A = __fadd_rn(sum_amp[p], A);
+        }
+        sum_pow[p] = P;
+        if (sum_amp) sum_amp[p] = A;
+        if (DA) {
+            // D_A exactly (amp_dispersion's operations) where it can be within
+            // the threshold; +inf where n SP - SA^2 exceeds (1.001 da_max SA)^2,
+            // a margin far above the rounding of either side, so that every
+            // pixel with exact D_A <= da_max keeps its value.
+            float d = __int_as_float(0x7f800000);
+            if (nz && A > 0.f) {
+                const float num2 = fmaxf(__fsub_rn(__fmul_rn(ps.n_eff, P), __fmul_rn(A, A)), 0.f);
+                const float lim = 1.001f * ps.da_max * A;
+                if (num2 <= lim * lim) d = amp_dispersion(P, A, ps.n_eff);
+            }
+            ps.da[p] = d;
+            if (d <= ps.da_max) ps.amp_new[p] = A_new;
         }
     }
 }
@@ -84,19 +111,36 @@ __global__ void __launch_bounds__(256) k_shp(const float *__restrict__ P, const 
     }
 }
 
-static int grid_for(long long work, int block) {
+// Grid-stride launches: one full wave of resident blocks (or fewer if the
+// work is smaller), so no partial second wave of equal-sized blocks.
+static int grid_for(long long work, int block, int per_sm = 8) {
     const int sms = device_sm_count();
     long long blocks = (work + block - 1) / block;
-    const long long cap = (long long)sms * 8;
+    const long long cap = (long long)sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     return (int)blocks;
 }
 
+template <class K>
+static int resident_per_sm(K kernel, int block) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
+
 cudaError_t launch_amp_stats(const float2 *z, int n, long long npix, float *sum_pow, float *sum_amp,
-                             int accumulate, cudaStream_t s) {
+                             int accumulate, cudaStream_t s, const PsStats *ps) {
     if (npix == 0) return cudaSuccess;
-    k_amp_stats<<<grid_for(npix, 256), 256, 0, s>>>(z, n, npix, sum_pow, sum_amp, accumulate);
+    if (ps && ps->da && ps->amp_new && sum_amp) {
+        static int per_sm = 0;  // per process: the kernel's residency does not change
+        if (per_sm == 0) per_sm = std::min(8, resident_per_sm(k_amp_stats<true>, 256));
+        k_amp_stats<true><<<grid_for(npix, 256, per_sm), 256, 0, s>>>(z, n, npix, sum_pow, sum_amp, accumulate,
+                                                                      *ps);
+    } else {
+        k_amp_stats<false><<<grid_for(npix, 256), 256, 0, s>>>(z, n, npix, sum_pow, sum_amp, accumulate,
+                                                               PsStats());
+    }
     return cudaGetLastError();
 }
 

@@ -47,8 +47,16 @@ __host__ __device__ inline int packed_index(int n, int i, int k) { return i * n 
 // ---------------------------------------------------------------- launches
 // Each returns cudaGetLastError() after the launch.
 // z: n contiguous planes of npix samples.
+// PS outputs of S1: D_A of the merged sums over n_eff images per pixel where
+// it is at most 1.001 da_max (+inf above that, where a new sample is zero or
+// where the amplitude sum is 0), and where D_A <= da_max the sum of |z| over
+// the new images (elsewhere amp_new is not written).
+struct PsStats {
+    float *da = nullptr, *amp_new = nullptr;
+    float n_eff = 0.f, da_max = 0.f;
+};
 cudaError_t launch_amp_stats(const float2 *z, int n, long long npix, float *sum_pow, float *sum_amp,
-                             int accumulate, cudaStream_t s);
+                             int accumulate, cudaStream_t s, const PsStats *ps = nullptr);
 cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *mask, uint16_t *count,
                        cudaStream_t s);
 // Returns cudaErrorInvalidConfiguration if the window/N combination exceeds
@@ -78,9 +86,26 @@ struct StackSource {
 cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, const EmiParams &prm,
                               float *phase, float *tcoh, float *lam, uint8_t *status, cudaStream_t s,
                               Prof *prof = nullptr, const StackSource *src = nullptr, const Schedule *sch = nullptr);
+// Persistent-scatterer selection inputs: D_A per pixel as S1 writes it (+inf
+// where a real sample is zero), the threshold and the mini-stack's reference
+// entry (da == nullptr: off).
+struct PsSelect {
+    const float *da = nullptr, *amp_new = nullptr;  // as S1 writes them (PsStats)
+    float da_max = 0.f;
+    int ref = 0;
+};
 // shift_date >= 0: the phases are re-referenced to that date (its phase subtracted).
+// ps on: each PS pixel is compressed on its own phases arg(z_i conj z_ref).
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
-                            float2 *kappa, cudaStream_t s, int shift_date = -1);
+                            float2 *kappa, cudaStream_t s, int shift_date = -1, const PsSelect &ps = PsSelect());
+
+// PS selection by amplitude dispersion and regridding onto the output grid:
+// phase [n - first_real][Ho][Wo] and status [Ho][Wo] updated in place.  D_A
+// from the merged sums (with the real samples checked), or, when da != nullptr,
+// read from the plane S1 wrote (sum_pow, sum_amp unused).
+cudaError_t launch_ps_regrid(const Planes &z, int n, int first_real, int ref, const Geom &g, const float *sum_pow,
+                             const float *sum_amp, int n_eff, float da_max, float *phase, uint8_t *status,
+                             cudaStream_t s, const float *da = nullptr);
 
 int device_sm_count();
 // Nonzero if a bounded device-side wait gave up since the last call (then cleared).

@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("PLK_LIB_PATH") or os.path.join(_HERE, "_build", "libplk.so")
 
 PLK_MAX_N = 32
-PX_EMI, PX_EMI_FP64, PX_EVD, PX_NODATA, PX_NOCONV = 0, 1, 2, 3, 4
+PX_EMI, PX_EMI_FP64, PX_EVD, PX_NODATA, PX_NOCONV, PX_PS = 0, 1, 2, 3, 4, 5
 _STATUS = {0: "PLK_OK", 1: "PLK_EINVAL", 2: "PLK_ENOMEM", 3: "PLK_ECUDA", 4: "PLK_ETIMEOUT", 5: "PLK_EUNSUPPORTED"}
 
 
@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_float), ("mu", ctypes.c_float),
                 ("tol", ctypes.c_float), ("max_iter", ctypes.c_int32), ("cond_max", ctypes.c_float),
                 ("fp64_resolve", ctypes.c_int32), ("err_max", ctypes.c_float), ("cov_precision", ctypes.c_int32),
-                ("ref_scheme", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("ref_scheme", ctypes.c_int32), ("ps_da_max", ctypes.c_float)]
 
 
 class StackDesc(ctypes.Structure):
@@ -75,6 +75,7 @@ _SIGS = {
     "plk_estimate_covariance": [_P, _P, _I, _I, _I, Window, _P, _I, _P],
     "plk_phase_link": [_P, _P, _I, ctypes.c_int64, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_compress": [_P, _P, _I, _I, _I, _I, Window, _P, _P],
+    "plk_ps_regrid": [_P, _P, _I, _I, _I, _I, Window, _P, _P, _I, _I, ctypes.c_float, _P, _P],
     "plk_state_create": [_P, _I, _I, Window, _I, _I, ctypes.POINTER(_P)],
     "plk_state_destroy": [_P],
     "plk_state_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -315,6 +316,25 @@ class Context:
                                   _ptr(kappa)), self.h)
         return kappa
 
+    def ps_regrid(self, slc: torch.Tensor, first_real: int, win, sum_pow: torch.Tensor, sum_amp: torch.Tensor,
+                  n_eff: int, ref: int, da_max: float, phase: torch.Tensor, status: torch.Tensor):
+        """PS cells of phase [N - first_real, Ho, Wo] and status [Ho, Wo] take
+        the phases of their lowest-D_A persistent scatterer (in place)."""
+        _need(slc, torch.complex64, "slc", self.device)
+        _need(sum_pow, torch.float32, "sum_pow", self.device)
+        _need(sum_amp, torch.float32, "sum_amp", self.device)
+        _need(phase, torch.float32, "phase", self.device)
+        _need(status, torch.uint8, "status", self.device)
+        N, H, W = slc.shape
+        Ho, Wo = output_shape(H, W, win)
+        if tuple(phase.shape) != (N - first_real, Ho, Wo) or tuple(status.shape) != (Ho, Wo) or \
+                tuple(sum_pow.shape) != (H, W) or tuple(sum_amp.shape) != (H, W):
+            raise ValueError("ps_regrid: shape mismatch")
+        _check(lib().plk_ps_regrid(self.h, _ptr(slc), N, int(first_real), H, W, window(win), _ptr(sum_pow),
+                                   _ptr(sum_amp), int(n_eff), int(ref), float(da_max), _ptr(phase), _ptr(status)),
+               self.h)
+        return phase, status
+
 
 class PhaseLinkFn(torch.autograd.Function):
     """phase = coherence -> EMI -> referenced phase of a stack, with the SHP
@@ -529,6 +549,10 @@ def phase_link(C, N, ref, params=None):
 
 def compress(slc, first_real, win, phase):
     return context(slc.device).compress(slc, first_real, win, phase)
+
+
+def ps_regrid(slc, first_real, win, sum_pow, sum_amp, n_eff, ref, da_max, phase, status):
+    return context(slc.device).ps_regrid(slc, first_real, win, sum_pow, sum_amp, n_eff, ref, da_max, phase, status)
 
 
 def ministack_step(state: State, new_slc, params=None):
