@@ -7,7 +7,8 @@ with the CUDA path (``paper_2511_12051_gb300``) and never imports it.
 The arithmetic lives in ``plk_oracle.c`` (plain C, double precision, one
 pixel at a time, each function citing the section of the paper it follows);
 this module only builds it with gcc, marshals numpy arrays and runs the
-mini-stack bookkeeping of Sec. II-B in ``chain.py``.
+mini-stack bookkeeping of Sec. II-B in ``chain.py``.  The phase cosine
+similarity of Sec. III-C is plain numpy in ``similarity.py``.
 
 Function pins (tests/test_oracle_*.py) tie every routine to something other
 than itself: closed forms, invariants, brute force on tiny inputs, a library
@@ -236,3 +237,4 @@ def ps_compress(z: np.ndarray, first_real: int, sum_pow: np.ndarray, sum_amp: np
 
 
 from .chain import OracleChain, ministack  # noqa: E402,F401
+from .similarity import disk_offsets, nearest3_pairs, phase_similarity  # noqa: E402,F401
