@@ -31,6 +31,7 @@ UNIT = "output px/s"
 WINDOW = (5, 11, 3, 6)  # wy, wx, sy, sx  ("11 x 5", strides 6 x 3)
 N_DATES = 15
 PS_DA_MAX = 0.2  # production PS threshold on the amplitude dispersion (Sec. IV)
+GS_RADIUS = 7    # gamma_s window radius in output pixels: ~200 m at the 30 m posting (Sec. III-C)
 H_FULL, W_FULL = 4096, 16384
 WORKLOAD = "burst-shaped mini-stack: N=15 complex64 SLCs x 4096x16384 px, 11x5 window, output strides 6x3"
 
@@ -70,6 +71,13 @@ def flops_emi(N: int, npx: int) -> float:
     the shifted Hadamard product ((8/3) N^3 each), ten inverse-iteration steps
     (8 N^2 each) and gamma_t (~10 N^2)."""
     return npx * ((16.0 / 3.0) * N ** 3 + 90.0 * N * N)
+
+
+def flops_similarity_pair(M: int) -> float:
+    """Algorithmic flops of one (pixel, neighbour) similarity over the nearest-3
+    network: per date the phasor product v_p conj(v_x) (6 flop) and three
+    network terms Re(w_b conj w_a) (4 flop each)."""
+    return 18.0 * M
 
 
 class ClockSampler:
@@ -513,6 +521,33 @@ def main():
         return {"value": npx * world * args.steps / (ms_alt / 1e3), "unit": UNIT, "ms_per_step": ms_alt / args.steps,
                 "kernels_ms_per_step": {kk: v[0] / args.steps for kk, v in kalt.items()}}
 
+    def time_similarity():
+        # gamma_s of the step's linked phases over the ~200 m window (radius 7 at the 30 m posting)
+        one_step()
+        ph = out["phase"]
+        gs = torch.empty((Ho, Wo), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                ctx.phase_similarity(ph, GS_RADIUS, gs)
+        torch.cuda.synchronize(dev)
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            h0.record(stream)
+            for _ in range(args.steps):
+                ctx.phase_similarity(ph, GS_RADIUS, gs)
+            h1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = h0.elapsed_time(h1) / args.steps
+        n_nb = len([1 for dy in range(-GS_RADIUS, GS_RADIUS + 1) for dx in range(-GS_RADIUS, GS_RADIUS + 1)
+                    if 0 < dy * dy + dx * dx <= GS_RADIUS ** 2])
+        flop = npx * n_nb * flops_similarity_pair(N_DATES)
+        return {"value": npx * world / (ms / 1e3), "unit": UNIT, "ms_per_call": ms, "radius": GS_RADIUS,
+                "neighbours": n_nb, "median_gamma_s": float(torch.nanmedian(gs).item()),
+                "roofline": {"bound": "alu", "achieved": flop / (ms / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                             "unit": "TFLOP/s", "frac": flop / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                             "work": "18 flop per date and neighbour (phasor product, three network terms)"}}
+
     modes = None
     if not args.no_modes and prec == plk.COV_FP32 and args.ps_da_max == 0:
         modes = {}
@@ -523,6 +558,7 @@ def main():
         modes["ps_regrid"]["ps_da_max"] = PS_DA_MAX
         modes["ps_regrid"]["ps_cells"] = int((out["status"] == plk.PX_PS).sum().item())
         modes["ps_regrid"]["output_cells"] = npx
+        modes["gamma_s"] = time_similarity()
 
     # ---------------------------------------------------------- CPU baseline
     cpu = None

@@ -292,6 +292,23 @@ plk_status plk_ps_regrid(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real
                          const float *sum_pow, const float *sum_amp, int n_eff, int ref_idx, float da_max,
                          float *phase, uint8_t *status);
 
+/* Phase cosine similarity gamma_s (Sec. III-C, eq. (phase-cosine-sim)).  For
+ * each output pixel p of the linked phases phase [M][Ho][Wo] (float, e.g. the
+ * real dates of a step's output) and each neighbour x of the disk
+ * dy^2 + dx^2 <= radius^2 (p itself excluded; neighbours outside the grid or
+ * with a non-finite phase left out):
+ *   s(p, x) = (1/N_ifg) sum cos((phi_b - phi_a)(p) - (phi_b - phi_a)(x))
+ * over the nearest-3 network, the pairs (a, b) with 1 <= b - a <= 3
+ * (N_ifg = 3M - 6 for M >= 3); gamma_s[p] = the median of s(p, x) over x (the
+ * mean of the two middle values for an even count), NaN where p has a
+ * non-finite phase or no neighbour is left.  gamma_s [Ho][Wo] float.  The
+ * paper's window is ~200 m (radius 7 at a 30 m posting).  2 <= M <= 32,
+ * 1 <= radius <= 32.  Errors: EINVAL; EUNSUPPORTED where the disk holds more
+ * than 512 neighbours (radius > 12) or the window and M exceed a CTA's shared
+ * memory; ECUDA. */
+plk_status plk_phase_similarity(plk_ctx *ctx, const float *phase, int M, int Ho, int Wo, int radius,
+                                float *gamma_s);
+
 /* ----------------------------------------------------------- adjoint */
 
 /* Scratch bytes plk_phase_link_backward needs for this stack and window. */

@@ -429,6 +429,24 @@ plk_status plk_ps_regrid(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real
     return PLK_OK;
 }
 
+plk_status plk_phase_similarity(plk_ctx *ctx, const float *phase, int M, int Ho, int Wo, int radius,
+                                float *gamma_s) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_phase_similarity: null ctx");
+    if (M < 2 || M > 32 || Ho < 0 || Wo < 0 || radius < 1 || radius > 32 || (long long)Ho * Wo >= (1LL << 31))
+        return fail(ctx, PLK_EINVAL, "plk_phase_similarity: bad argument");
+    if ((long long)Ho * Wo == 0) return PLK_OK;
+    if (!phase || !gamma_s) return fail(ctx, PLK_EINVAL, "plk_phase_similarity: null pointer");
+    if (!aligned(phase, 4) || !aligned(gamma_s, 4)) return fail(ctx, PLK_EINVAL, "plk_phase_similarity: misaligned pointer");
+    DeviceGuard dg(ctx->device);
+    ctx->prof.begin("phase_similarity", ctx->stream);
+    cudaError_t e = plk::launch_phase_similarity(phase, M, Ho, Wo, radius, gamma_s, ctx->stream);
+    ctx->prof.end(ctx->stream);
+    if (e == cudaErrorInvalidConfiguration)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_phase_similarity: radius %d with M=%d exceeds shared memory", radius, M);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_phase_similarity");
+    return PLK_OK;
+}
+
 // ----------------------------------------------------------------- adjoint
 
 plk_status plk_backward_workspace_size(int N, int H, int W, plk_window win, size_t *bytes) {

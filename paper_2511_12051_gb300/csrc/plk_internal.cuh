@@ -107,6 +107,12 @@ cudaError_t launch_ps_regrid(const Planes &z, int n, int first_real, int ref, co
                              const float *sum_amp, int n_eff, float da_max, float *phase, uint8_t *status,
                              cudaStream_t s, const float *da = nullptr);
 
+// Phase cosine similarity gamma_s of linked phases [M][Ho][Wo] over a disk of
+// radius r; cudaErrorInvalidConfiguration if no tile fits in shared memory.
+cudaError_t launch_phase_similarity(const float *phase, int M, int Ho, int Wo, int r, float *gamma_s,
+                                    cudaStream_t s);
+int phase_sim_disk_count(int r);
+
 int device_sm_count();
 // Nonzero if a bounded device-side wait gave up since the last call (then cleared).
 // Adjoint of S3-S5 (masks frozen): scratch bytes and the launch sequence

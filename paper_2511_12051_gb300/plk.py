@@ -76,6 +76,7 @@ _SIGS = {
     "plk_phase_link": [_P, _P, _I, ctypes.c_int64, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_compress": [_P, _P, _I, _I, _I, _I, Window, _P, _P],
     "plk_ps_regrid": [_P, _P, _I, _I, _I, _I, Window, _P, _P, _I, _I, ctypes.c_float, _P, _P],
+    "plk_phase_similarity": [_P, _P, _I, _I, _I, _I, _P],
     "plk_state_create": [_P, _I, _I, Window, _I, _I, ctypes.POINTER(_P)],
     "plk_state_destroy": [_P],
     "plk_state_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -316,6 +317,18 @@ class Context:
                                   _ptr(kappa)), self.h)
         return kappa
 
+    def phase_similarity(self, phase: torch.Tensor, radius: int, out: torch.Tensor | None = None):
+        """gamma_s [Ho, Wo] of linked phases [M, Ho, Wo] over a disk of `radius` output pixels."""
+        _need(phase, torch.float32, "phase", self.device)
+        M, Ho, Wo = phase.shape
+        if out is None:
+            out = torch.empty((Ho, Wo), dtype=torch.float32, device=self.device)
+        _need(out, torch.float32, "gamma_s", self.device)
+        if tuple(out.shape) != (Ho, Wo):
+            raise ValueError("phase_similarity: output shape mismatch")
+        _check(lib().plk_phase_similarity(self.h, _ptr(phase), M, Ho, Wo, int(radius), _ptr(out)), self.h)
+        return out
+
     def ps_regrid(self, slc: torch.Tensor, first_real: int, win, sum_pow: torch.Tensor, sum_amp: torch.Tensor,
                   n_eff: int, ref: int, da_max: float, phase: torch.Tensor, status: torch.Tensor):
         """PS cells of phase [N - first_real, Ho, Wo] and status [Ho, Wo] take
@@ -549,6 +562,10 @@ def phase_link(C, N, ref, params=None):
 
 def compress(slc, first_real, win, phase):
     return context(slc.device).compress(slc, first_real, win, phase)
+
+
+def phase_similarity(phase, radius, out=None):
+    return context(phase.device).phase_similarity(phase, radius, out)
 
 
 def ps_regrid(slc, first_real, win, sum_pow, sum_amp, n_eff, ref, da_max, phase, status):
