@@ -8,7 +8,8 @@ The arithmetic lives in ``plk_oracle.c`` (plain C, double precision, one
 pixel at a time, each function citing the section of the paper it follows);
 this module only builds it with gcc, marshals numpy arrays and runs the
 mini-stack bookkeeping of Sec. II-B in ``chain.py``.  The phase cosine
-similarity of Sec. III-C is plain numpy in ``similarity.py``.
+similarity of Sec. III-C is plain numpy in ``similarity.py``, the L1 network
+inversion by ADMM (Sec. III-E, Appendix) numpy and scipy in ``inversion.py``.
 
 Function pins (tests/test_oracle_*.py) tie every routine to something other
 than itself: closed forms, invariants, brute force on tiny inputs, a library
@@ -238,3 +239,4 @@ def ps_compress(z: np.ndarray, first_real: int, sum_pow: np.ndarray, sum_amp: np
 
 from .chain import OracleChain, ministack  # noqa: E402,F401
 from .similarity import disk_offsets, nearest3_pairs, phase_similarity  # noqa: E402,F401
+from .inversion import incidence, l1_invert, soft_threshold  # noqa: E402,F401
