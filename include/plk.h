@@ -309,6 +309,26 @@ plk_status plk_ps_regrid(plk_ctx *ctx, const plk_c64 *slc, int N, int first_real
 plk_status plk_phase_similarity(plk_ctx *ctx, const float *phase, int M, int Ho, int Wo, int radius,
                                 float *gamma_s);
 
+/* L1 time-series network inversion by ADMM (Sec. III-E, eq. (l1-min);
+ * Appendix).  Per pixel p, with b = unw[k][p] the unwrapped phase of
+ * interferogram k = (pairs[2k], pairs[2k+1]) = (a, b), a < b, and x the
+ * phase series of dates 1..n_dates-1 relative to date 0, minimise
+ * ||A x - b||_1 (A: -1 at date a, +1 at date b) by the ADMM iteration
+ *   x = (A^T A)^{-1} A^T (b + z - u),  z = S_{1/rho}(A x - b + u),
+ *   u = u + A x - b - z,
+ * from z = u = 0, exactly `iters` iterations, in single precision (the
+ * Cholesky factor of A^T A, shared by all pixels, in double on the host).
+ * Networks: any set of distinct pairs with b - a <= 3 (the nearest-3 network
+ * of Sec. III-D and its subsets) that determines every date; n_dates <= 17.
+ * unw [n_ifg][npx] float (device); pairs [n_ifg][2] int32 (host); x
+ * [n_dates-1][npx] float; residual [n_ifg][npx] float = b - A x (may be NULL:
+ * residuals far from 2 pi k mark unwrapping errors, Sec. III-E).  rho > 0,
+ * 1 <= iters <= 100000.  Errors: EINVAL (bad pair, repeated pair, a network
+ * that leaves a date undetermined); EUNSUPPORTED (b - a > 3, n_dates > 17);
+ * ECUDA. */
+plk_status plk_invert_l1(plk_ctx *ctx, const float *unw, int n_dates, const int32_t *pairs, int n_ifg, int64_t npx,
+                         float rho, int iters, float *x, float *residual);
+
 /* ----------------------------------------------------------- adjoint */
 
 /* Scratch bytes plk_phase_link_backward needs for this stack and window. */

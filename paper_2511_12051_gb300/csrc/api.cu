@@ -447,6 +447,72 @@ plk_status plk_phase_similarity(plk_ctx *ctx, const float *phase, int M, int Ho,
     return PLK_OK;
 }
 
+plk_status plk_invert_l1(plk_ctx *ctx, const float *unw, int n_dates, const int32_t *pairs, int n_ifg, int64_t npx,
+                         float rho, int iters, float *x, float *residual) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_invert_l1: null ctx");
+    if (n_dates < 2 || n_ifg < 1 || npx < 0 || !pairs || !(rho > 0.f && rho < 1e30f) || iters < 1 ||
+        iters > 100000)
+        return fail(ctx, PLK_EINVAL, "plk_invert_l1: bad argument");
+    if (n_dates > 17)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_invert_l1: %d dates (at most 17 are supported)", n_dates);
+    const int nx = n_dates - 1, nxp = nx <= 8 ? 8 : 16;
+    plk::AdmmNet net;
+    for (int s = 0; s < 48; ++s) net.plane[s] = -1;
+    double G[16][16] = {};  // A^T A
+    for (int k = 0; k < n_ifg; ++k) {
+        const int a = pairs[2 * k], b = pairs[2 * k + 1];
+        if (a < 0 || b >= n_dates || b <= a)
+            return fail(ctx, PLK_EINVAL, "plk_invert_l1: pair %d = (%d, %d) is not 0 <= a < b < n_dates", k, a, b);
+        if (b - a > 3)
+            return fail(ctx, PLK_EUNSUPPORTED, "plk_invert_l1: pair %d = (%d, %d) is outside the nearest-3 network",
+                        k, a, b);
+        const int s = (b - a - 1) * nxp + a;
+        if (net.plane[s] >= 0) return fail(ctx, PLK_EINVAL, "plk_invert_l1: pair (%d, %d) repeated", a, b);
+        net.plane[s] = k;
+        // row of A: -1 at date a, +1 at date b (date 0 dropped)
+        const int ia = a - 1, ib = b - 1;
+        G[ib][ib] += 1.0;
+        if (ia >= 0) {
+            G[ia][ia] += 1.0;
+            G[ia][ib] -= 1.0;
+            G[ib][ia] -= 1.0;
+        }
+    }
+    // Banded Cholesky of A^T A (bandwidth 3 for these networks), identity beyond nx.
+    double L[16][16] = {};
+    for (int i = 0; i < nx; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double sum = G[i][j];
+            for (int q = 0; q < j; ++q) sum -= L[i][q] * L[j][q];
+            if (i == j) {
+                if (!(sum > 1e-9))
+                    return fail(ctx, PLK_EINVAL, "plk_invert_l1: the network does not determine date %d", i + 1);
+                L[i][i] = sqrt(sum);
+            } else {
+                L[i][j] = sum / L[j][j];
+            }
+        }
+    }
+    for (int i = 0; i < 16; ++i) {
+        net.L[i][0] = i < nx ? (float)(1.0 / L[i][i]) : 1.f;
+        for (int q = 1; q <= 3; ++q) net.L[i][q] = (i < nx && i - q >= 0) ? (float)L[i][i - q] : 0.f;
+    }
+    net.kappa = 1.0f / rho;
+    net.iters = iters;
+    net.nx = nx;
+    net.nxp = nxp;
+    if (npx == 0) return PLK_OK;
+    if (!unw || !x) return fail(ctx, PLK_EINVAL, "plk_invert_l1: null pointer");
+    if (!aligned(unw, 4) || !aligned(x, 4) || (residual && !aligned(residual, 4)))
+        return fail(ctx, PLK_EINVAL, "plk_invert_l1: misaligned pointer");
+    DeviceGuard dg(ctx->device);
+    ctx->prof.begin("invert_l1", ctx->stream);
+    cudaError_t e = plk::launch_admm_l1(unw, npx, net, x, residual, ctx->stream);
+    ctx->prof.end(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_invert_l1");
+    return PLK_OK;
+}
+
 // ----------------------------------------------------------------- adjoint
 
 plk_status plk_backward_workspace_size(int N, int H, int W, plk_window win, size_t *bytes) {

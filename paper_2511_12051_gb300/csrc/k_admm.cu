@@ -1,0 +1,108 @@
+// L1 time-series network inversion by ADMM (Sec. III-E, eq. (l1-min);
+// Appendix): per pixel, minimise ||A x - b||_1 over the phase series x
+// relative to the first date, b the unwrapped phases of the network's
+// interferograms, by
+//   x <- (A^T A)^{-1} A^T (b + z - u),  t = A x - b + u,
+//   z <- S_{1/rho}(t),                  u <- t - z  (= clamp(t, -1/rho, 1/rho)),
+// from z = u = 0, a fixed number of iterations.
+//
+// One thread per pixel, every quantity in registers.  The networks are
+// subsets of the nearest-3 network (pairs (a, a + d), d <= 3), so each pair
+// has a compile-time slot (d - 1) * NXP + a: A x and A^T v are fixed register
+// arithmetic, and A^T A is banded (bandwidth 3), its Cholesky factor L
+// computed once on the host in double precision and passed in the parameter
+// space; the solve is a banded forward and back substitution (4 FMA a row
+// each way).  Slots the caller's network does not hold are masked (their v
+// is zero), so they never reach x.  Each slot's b is read from the caller's
+// interferogram plane by a uniform index (coalesced across the warp).
+#include "plk_internal.cuh"
+
+namespace plk {
+
+template <int NXP>
+__global__ void __launch_bounds__(128) k_admm_l1(const float *__restrict__ unw, long long npx,
+                                                 const __grid_constant__ AdmmNet net, float *__restrict__ x_out,
+                                                 float *__restrict__ resid) {
+    constexpr int NS = 3 * NXP;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npx; p += stride) {
+        float b[NS], u[NS], x[NXP], w[NXP];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            b[s] = net.plane[s] >= 0 ? __ldg(unw + net.plane[s] * npx + p) : 0.f;
+            u[s] = 0.f;
+        }
+        // v = b + z - u = b at the start
+#pragma unroll
+        for (int i = 0; i < NXP; ++i) w[i] = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int d = s / NXP + 1, a = s % NXP;
+            if (a + d - 1 < NXP) w[a + d - 1] += b[s];
+            if (a >= 1) w[a - 1] -= b[s];
+        }
+        for (int it = 0; it < net.iters; ++it) {
+            // x = (A^T A)^{-1} w: L y = w, then L^T x = y (L banded, stored by band).
+#pragma unroll
+            for (int i = 0; i < NXP; ++i) {
+                float acc = w[i];
+#pragma unroll
+                for (int k = 1; k <= 3; ++k)
+                    if (i - k >= 0) acc -= net.L[i][k] * x[i - k];
+                x[i] = acc * net.L[i][0];
+            }
+#pragma unroll
+            for (int i = NXP - 1; i >= 0; --i) {
+                float acc = x[i];
+#pragma unroll
+                for (int k = 1; k <= 3; ++k)
+                    if (i + k < NXP) acc -= net.L[i + k][k] * x[i + k];
+                x[i] = acc * net.L[i][0];
+            }
+            // t = A x - b + u;  u = clamp(t);  v = b + z - u = b + t - 2u;  w = A^T v
+#pragma unroll
+            for (int i = 0; i < NXP; ++i) w[i] = 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int d = s / NXP + 1, a = s % NXP;
+                if (net.plane[s] >= 0) {  // uniform: the same network for every pixel
+                    const float ax = (a + d - 1 < NXP ? x[a + d - 1] : 0.f) - (a >= 1 ? x[a - 1] : 0.f);
+                    const float t = ax - b[s] + u[s];
+                    u[s] = fminf(fmaxf(t, -net.kappa), net.kappa);
+                    const float v = b[s] + t - 2.f * u[s];
+                    if (a + d - 1 < NXP) w[a + d - 1] += v;
+                    if (a >= 1) w[a - 1] -= v;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NXP; ++i)
+            if (i < net.nx) x_out[i * npx + p] = x[i];
+        if (resid) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int d = s / NXP + 1, a = s % NXP;
+                if (net.plane[s] >= 0) {
+                    const float ax = (a + d - 1 < NXP ? x[a + d - 1] : 0.f) - (a >= 1 ? x[a - 1] : 0.f);
+                    resid[net.plane[s] * npx + p] = b[s] - ax;
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_admm_l1(const float *unw, long long npx, const AdmmNet &net, float *x, float *resid,
+                           cudaStream_t s) {
+    if (npx == 0) return cudaSuccess;
+    const long long want = (npx + 127) / 128;
+    auto kern = net.nxp == 8 ? k_admm_l1<8> : k_admm_l1<16>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const long long cap = (long long)device_sm_count() * per_sm;
+    kern<<<(unsigned)(want < cap ? want : cap), 128, 0, s>>>(unw, npx, net, x, resid);
+    return cudaGetLastError();
+}
+
+}  // namespace plk

@@ -77,6 +77,7 @@ _SIGS = {
     "plk_compress": [_P, _P, _I, _I, _I, _I, Window, _P, _P],
     "plk_ps_regrid": [_P, _P, _I, _I, _I, _I, Window, _P, _P, _I, _I, ctypes.c_float, _P, _P],
     "plk_phase_similarity": [_P, _P, _I, _I, _I, _I, _P],
+    "plk_invert_l1": [_P, _P, _I, _P, _I, ctypes.c_int64, ctypes.c_float, _I, _P, _P],
     "plk_state_create": [_P, _I, _I, Window, _I, _I, ctypes.POINTER(_P)],
     "plk_state_destroy": [_P],
     "plk_state_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -329,6 +330,21 @@ class Context:
         _check(lib().plk_phase_similarity(self.h, _ptr(phase), M, Ho, Wo, int(radius), _ptr(out)), self.h)
         return out
 
+    def invert_l1(self, unw: torch.Tensor, n_dates: int, pairs, rho: float = 1.0, iters: int = 50,
+                  residual: bool = False):
+        """x [n_dates-1, ...] (and b - A x) of unwrapped phases unw [n_ifg, ...] by L1 ADMM."""
+        _need(unw, torch.float32, "unw", self.device)
+        n_ifg = unw.shape[0]
+        npx = unw[0].numel() if n_ifg else 0
+        pr = (ctypes.c_int32 * (2 * len(pairs)))(*[int(v) for ab in pairs for v in ab])
+        if len(pairs) != n_ifg:
+            raise ValueError("invert_l1: one pair per interferogram plane")
+        x = torch.empty((n_dates - 1,) + tuple(unw.shape[1:]), dtype=torch.float32, device=self.device)
+        r = torch.empty_like(unw) if residual else None
+        _check(lib().plk_invert_l1(self.h, _ptr(unw), int(n_dates), ctypes.cast(pr, ctypes.c_void_p), n_ifg, npx,
+                                   float(rho), int(iters), _ptr(x), _ptr(r)), self.h)
+        return (x, r) if residual else x
+
     def ps_regrid(self, slc: torch.Tensor, first_real: int, win, sum_pow: torch.Tensor, sum_amp: torch.Tensor,
                   n_eff: int, ref: int, da_max: float, phase: torch.Tensor, status: torch.Tensor):
         """PS cells of phase [N - first_real, Ho, Wo] and status [Ho, Wo] take
@@ -562,6 +578,10 @@ def phase_link(C, N, ref, params=None):
 
 def compress(slc, first_real, win, phase):
     return context(slc.device).compress(slc, first_real, win, phase)
+
+
+def invert_l1(unw, n_dates, pairs, rho=1.0, iters=50, residual=False):
+    return context(unw.device).invert_l1(unw, n_dates, pairs, rho, iters, residual)
 
 
 def phase_similarity(phase, radius, out=None):
