@@ -6,7 +6,10 @@
 //   z <- S_{1/rho}(t),                  u <- t - z  (= clamp(t, -1/rho, 1/rho)),
 // from z = u = 0, a fixed number of iterations.
 //
-// One thread per pixel, every quantity in registers.  The networks are
+// One thread per pixel: x, A^T v and u in registers, b in shared memory
+// (column threadIdx.x of a [slot][128] array: every access of a warp is
+// conflict-free), which leaves 96 registers a thread and 5 CTAs an SM.  The
+// networks are
 // subsets of the nearest-3 network (pairs (a, a + d), d <= 3), so each pair
 // has a compile-time slot (d - 1) * NXP + a: A x and A^T v are fixed register
 // arithmetic, and A^T A is banded (bandwidth 3), its Cholesky factor L
@@ -19,27 +22,28 @@
 
 namespace plk {
 
+constexpr int kAdmmThreads = 128;
+
 template <int NXP>
-__global__ void __launch_bounds__(128) k_admm_l1(const float *__restrict__ unw, long long npx,
-                                                 const __grid_constant__ AdmmNet net, float *__restrict__ x_out,
-                                                 float *__restrict__ resid) {
+__global__ void __launch_bounds__(kAdmmThreads) k_admm_l1(const float *__restrict__ unw, long long npx,
+                                                 const __grid_constant__ AdmmNet net, float *__restrict__ x_out) {
     constexpr int NS = 3 * NXP;
+    extern __shared__ float b_sh[];  // [NS][kAdmmThreads]
+    float *b = b_sh + threadIdx.x;   // b[s * kAdmmThreads]: this thread's slot s
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npx; p += stride) {
-        float b[NS], u[NS], x[NXP], w[NXP];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            b[s] = net.plane[s] >= 0 ? __ldg(unw + net.plane[s] * npx + p) : 0.f;
-            u[s] = 0.f;
-        }
+        float u[NS], x[NXP], w[NXP];
         // v = b + z - u = b at the start
 #pragma unroll
         for (int i = 0; i < NXP; ++i) w[i] = 0.f;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int d = s / NXP + 1, a = s % NXP;
-            if (a + d - 1 < NXP) w[a + d - 1] += b[s];
-            if (a >= 1) w[a - 1] -= b[s];
+            const float bv = net.plane[s] >= 0 ? __ldg(unw + net.plane[s] * npx + p) : 0.f;
+            b[s * kAdmmThreads] = bv;
+            u[s] = 0.f;
+            if (a + d - 1 < NXP) w[a + d - 1] += bv;
+            if (a >= 1) w[a - 1] -= bv;
         }
         for (int it = 0; it < net.iters; ++it) {
             // x = (A^T A)^{-1} w: L y = w, then L^T x = y (L banded, stored by band).
@@ -67,9 +71,10 @@ __global__ void __launch_bounds__(128) k_admm_l1(const float *__restrict__ unw, 
                 const int d = s / NXP + 1, a = s % NXP;
                 if (net.plane[s] >= 0) {  // uniform: the same network for every pixel
                     const float ax = (a + d - 1 < NXP ? x[a + d - 1] : 0.f) - (a >= 1 ? x[a - 1] : 0.f);
-                    const float t = ax - b[s] + u[s];
+                    const float bs = b[s * kAdmmThreads];
+                    const float t = ax - bs + u[s];
                     u[s] = fminf(fmaxf(t, -net.kappa), net.kappa);
-                    const float v = b[s] + t - 2.f * u[s];
+                    const float v = bs + t - 2.f * u[s];
                     if (a + d - 1 < NXP) w[a + d - 1] += v;
                     if (a >= 1) w[a - 1] -= v;
                 }
@@ -78,15 +83,22 @@ __global__ void __launch_bounds__(128) k_admm_l1(const float *__restrict__ unw, 
 #pragma unroll
         for (int i = 0; i < NXP; ++i)
             if (i < net.nx) x_out[i * npx + p] = x[i];
-        if (resid) {
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                const int d = s / NXP + 1, a = s % NXP;
-                if (net.plane[s] >= 0) {
-                    const float ax = (a + d - 1 < NXP ? x[a + d - 1] : 0.f) - (a >= 1 ? x[a - 1] : 0.f);
-                    resid[net.plane[s] * npx + p] = b[s] - ax;
-                }
-            }
+    }
+}
+
+// Residual b - A x of every interferogram, a separate streaming pass (kept out
+// of the solve, whose register budget it would otherwise double).
+__global__ void __launch_bounds__(256) k_admm_residual(const float *__restrict__ unw, long long npx,
+                                                       const __grid_constant__ AdmmNet net,
+                                                       const float *__restrict__ x, float *__restrict__ resid) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npx; p += stride) {
+        for (int s = 0; s < 3 * net.nxp; ++s) {
+            if (net.plane[s] < 0) continue;  // uniform
+            const int d = s / net.nxp + 1, a = s % net.nxp;
+            const float xb = a + d - 1 < net.nx ? __ldg(x + (long long)(a + d - 1) * npx + p) : 0.f;
+            const float xa = a >= 1 ? __ldg(x + (long long)(a - 1) * npx + p) : 0.f;
+            resid[net.plane[s] * npx + p] = __ldg(unw + net.plane[s] * npx + p) - (xb - xa);
         }
     }
 }
@@ -94,14 +106,19 @@ __global__ void __launch_bounds__(128) k_admm_l1(const float *__restrict__ unw, 
 cudaError_t launch_admm_l1(const float *unw, long long npx, const AdmmNet &net, float *x, float *resid,
                            cudaStream_t s) {
     if (npx == 0) return cudaSuccess;
-    const long long want = (npx + 127) / 128;
+    const long long want = (npx + kAdmmThreads - 1) / kAdmmThreads;
     auto kern = net.nxp == 8 ? k_admm_l1<8> : k_admm_l1<16>;
+    const size_t smem = (size_t)3 * net.nxp * kAdmmThreads * sizeof(float);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdmmThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const long long cap = (long long)device_sm_count() * per_sm;
-    kern<<<(unsigned)(want < cap ? want : cap), 128, 0, s>>>(unw, npx, net, x, resid);
+    kern<<<(unsigned)(want < cap ? want : cap), kAdmmThreads, smem, s>>>(unw, npx, net, x);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !resid) return e;
+    const long long rwant = (npx + 255) / 256, rcap = (long long)device_sm_count() * 8;
+    k_admm_residual<<<(unsigned)(rwant < rcap ? rwant : rcap), 256, 0, s>>>(unw, npx, net, x, resid);
     return cudaGetLastError();
 }
 
