@@ -4,9 +4,10 @@
 // the sum over the nearest-3 network of the M dates (1 <= b - a <= 3).
 //
 // With unit phasors v = e^{j phi} and w_i = v_i(p) conj(v_i(x)), each term is
-// Re(w_b conj(w_a)), so one pass over the dates with the last three w in
-// registers gives the three diagonals of the network: 10 FMA per date and
-// neighbour, the centre's phasors held in registers.
+// Re(w_b conj(w_a)), so one pass over the dates with w in registers gives the
+// three diagonals of the network: per date and neighbour, 4 scalar operations
+// for w and 3 packed FP32x2 fused multiply-adds (fma.rn.f32x2) for the terms,
+// the centre's phasors held in registers.
 //
 // A CTA owns a TY x TX tile of output pixels and holds the tile plus an
 // r-pixel halo as phasors in shared memory, pixel-major: one record of S
@@ -27,6 +28,7 @@
 
 #include <algorithm>
 
+#include "f32x2.cuh"
 #include "plk_internal.cuh"
 
 namespace plk {
@@ -39,6 +41,7 @@ __device__ __forceinline__ uint32_t order_key(float v) {
 __device__ __forceinline__ float key_value(uint32_t k) {
     return __uint_as_float(k ^ ((k >> 31) ? 0x80000000u : 0xffffffffu));
 }
+
 
 constexpr int kSimHole = -0x7fffffff;  // an unused slot of the neighbour list
 
@@ -116,25 +119,25 @@ __global__ void __launch_bounds__(512) k_phase_sim(const float *__restrict__ pha
                 const int o = j < nlist ? off[j] : kSimHole;
                 if (o != kSimHole && ok) {
                     const float4 *nb = reinterpret_cast<const float4 *>(ctr + o);
-                    float2 w[MP];
+                    unsigned long long w[MP];  // w = v_p conj(v_x), packed (re, im)
 #pragma unroll
                     for (int q = 0; q < MP / 2; ++q) {
                         const float4 x2 = nb[q];
-                        // w = v_p conj(v_x)
-                        w[2 * q] = make_float2(vp[2 * q].x * x2.x + vp[2 * q].y * x2.y,
-                                               vp[2 * q].y * x2.x - vp[2 * q].x * x2.y);
-                        w[2 * q + 1] = make_float2(vp[2 * q + 1].x * x2.z + vp[2 * q + 1].y * x2.w,
-                                                   vp[2 * q + 1].y * x2.z - vp[2 * q + 1].x * x2.w);
+                        w[2 * q] = pack2(fmaf(vp[2 * q].x, x2.x, vp[2 * q].y * x2.y),
+                                         fmaf(vp[2 * q].y, x2.x, -vp[2 * q].x * x2.y));
+                        w[2 * q + 1] = pack2(fmaf(vp[2 * q + 1].x, x2.z, vp[2 * q + 1].y * x2.w),
+                                             fmaf(vp[2 * q + 1].y, x2.z, -vp[2 * q + 1].x * x2.w));
                     }
-                    // the network terms Re(w_i conj(w_{i-d})), d = 1..3, one accumulator per d
-                    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                    // the network terms Re(w_i conj(w_{i-d})) = w_i.re w_j.re + w_i.im w_j.im,
+                    // d = 1..3: one packed accumulator per d, halves added at the end
+                    unsigned long long a1 = 0ull, a2 = 0ull, a3 = 0ull;  // (0.f, 0.f)
 #pragma unroll
                     for (int i = 1; i < MP; ++i) {
-                        a1 += w[i].x * w[i - 1].x + w[i].y * w[i - 1].y;
-                        if (i >= 2) a2 += w[i].x * w[i - 2].x + w[i].y * w[i - 2].y;
-                        if (i >= 3) a3 += w[i].x * w[i - 3].x + w[i].y * w[i - 3].y;
+                        a1 = fma2(w[i], w[i - 1], a1);
+                        if (i >= 2) a2 = fma2(w[i], w[i - 2], a2);
+                        if (i >= 3) a3 = fma2(w[i], w[i - 3], a3);
                     }
-                    const float acc = a1 + a2 + a3;
+                    const float acc = hsum2(a1) + hsum2(a2) + hsum2(a3);
                     if (!isnan(acc)) {
                         key[u] = order_key(acc);
                         ++nv;
