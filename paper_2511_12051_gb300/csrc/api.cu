@@ -455,7 +455,9 @@ plk_status plk_invert_l1(plk_ctx *ctx, const float *unw, int n_dates, const int3
         return fail(ctx, PLK_EINVAL, "plk_invert_l1: bad argument");
     if (n_dates > 17)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_invert_l1: %d dates (at most 17 are supported)", n_dates);
-    const int nx = n_dates - 1, nxp = nx <= 8 ? 8 : 16;
+    const int nx = n_dates - 1;
+    const int nxp = nx <= 4 ? 4 : nx <= 8 ? 8 : nx <= 12 ? 12 : nx;  // instantiated sizes: 4, 8, 12, 14, 15, 16
+    if (nxp < 1) return fail(ctx, PLK_EINVAL, "plk_invert_l1: bad argument");
     plk::AdmmNet net;
     for (int s = 0; s < 48; ++s) net.plane[s] = -1;
     double G[16][16] = {};  // A^T A
@@ -466,7 +468,7 @@ plk_status plk_invert_l1(plk_ctx *ctx, const float *unw, int n_dates, const int3
         if (b - a > 3)
             return fail(ctx, PLK_EUNSUPPORTED, "plk_invert_l1: pair %d = (%d, %d) is outside the nearest-3 network",
                         k, a, b);
-        const int s = (b - a - 1) * nxp + a;
+        const int s = plk::admm_slot(nxp, b - a, a);
         if (net.plane[s] >= 0) return fail(ctx, PLK_EINVAL, "plk_invert_l1: pair (%d, %d) repeated", a, b);
         net.plane[s] = k;
         // row of A: -1 at date a, +1 at date b (date 0 dropped)

@@ -113,16 +113,21 @@ cudaError_t launch_phase_similarity(const float *phase, int M, int Ho, int Wo, i
                                     cudaStream_t s);
 int phase_sim_disk_count(int r);
 
-// A network inside the nearest-3 network for the ADMM inversion: slot
-// (d - 1) * nxp + a holds pair (a, a + d), d <= 3; plane[slot] is the caller's
-// interferogram index (-1: not in the network).  L[i] = {1 / L_ii, L_i,i-1,
-// L_i,i-2, L_i,i-3}: the banded Cholesky factor of A^T A (identity beyond nx).
+// A network inside the nearest-3 network for the ADMM inversion over nxp
+// unknown dates: slot admm_slot(nxp, d, a) holds pair (a, a + d), d <= 3,
+// a + d <= nxp (3 nxp - 3 slots); plane[slot] is the caller's interferogram
+// index (-1: not in the network).  L[i] =
+// {1 / L_ii, L_i,i-1, L_i,i-2, L_i,i-3}: the banded Cholesky factor of A^T A
+// (identity beyond nx).
 struct AdmmNet {
     int plane[48];
     float L[16][4];
     float kappa;  // 1 / rho
     int iters, nx, nxp;
 };
+__host__ __device__ constexpr int admm_slot(int nxp, int d, int a) {
+    return (d - 1) * nxp - (d - 1) * (d - 2) / 2 + a;
+}
 cudaError_t launch_admm_l1(const float *unw, long long npx, const AdmmNet &net, float *x, float *resid,
                            cudaStream_t s);
 
