@@ -8,7 +8,8 @@
 //
 // One thread per pixel: x, A^T v and u in registers, b in shared memory
 // (column threadIdx.x of a [slot][128] array: every access of a warp is
-// conflict-free), which leaves about 90 registers a thread and 5 CTAs an SM.
+// conflict-free); at most 128 registers a thread (4 CTAs an SM: with fewer
+// registers the complete-network variant spills, and runs 28% slower).
 // The networks are subsets of the nearest-3 network (pairs (a, a + d),
 // d <= 3), so each pair has a compile-time slot admm_slot(NXP, d, a), NXP the
 // number of unknown dates rounded up to an instantiated size: A x and A^T v
@@ -30,7 +31,7 @@ constexpr int kAdmmThreads = 128;
 // dates (no slot is masked, no branch); otherwise slots outside the network
 // are skipped by a branch that is uniform across the grid.
 template <int NXP, bool FULL>
-__global__ void __launch_bounds__(kAdmmThreads, 5) k_admm_l1(const float *__restrict__ unw, long long npx,
+__global__ void __launch_bounds__(kAdmmThreads, 4) k_admm_l1(const float *__restrict__ unw, long long npx,
                                                  const __grid_constant__ AdmmNet net, float *__restrict__ x_out) {
     constexpr int NS = 3 * NXP - 3;
     extern __shared__ float b_sh[];  // [NS][kAdmmThreads]
