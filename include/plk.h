@@ -269,6 +269,21 @@ plk_status plk_state_load(plk_ctx *ctx, const char *path, int M_max, plk_state *
 plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
                               const plk_params *params, float *phase, float *tcoh,
                               uint8_t *status, uint16_t *shp_count);
+/* S1-S8 from host memory: plk_ministack_step with the new SLCs read from host
+ * memory new_slc [M][H][W] and the outputs phase [M][Ho][Wo], tcoh and status
+ * [Ho][Wo] (shp_count may be NULL) written to host memory.  Asynchronous: it
+ * returns once the work is enqueued; the host buffers must stay untouched
+ * until plk_sync(ctx).  The SLCs go to one of two device staging buffers on a
+ * copy stream of the library's own, so a call's copy overlaps the previous
+ * call's compute (with pinned host memory; pageable memory works but copies
+ * synchronously).  The first call allocates the two staging buffers (M_max
+ * planes each) and the device outputs; plk_state_destroy releases them.
+ * Errors: EINVAL, ENOMEM, ECUDA, and those of plk_ministack_step.  Not part
+ * of the paper's method: a transfer schedule around it. */
+plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
+                                   const plk_params *params, float *phase, float *tcoh, uint8_t *status,
+                                   uint16_t *shp_count);
+
 
 /* ------------------------------------------ persistent scatterers */
 

@@ -25,6 +25,21 @@ struct plk_state {
     uint16_t *count;     // [Ho][Wo]
     float2 *C;           // [Ho*Wo][ntri(K_max+M_max)]
     float *phase_all;    // [K_max+M_max][Ho][Wo]
+    // plk_ministack_step_host: two device staging buffers for the new SLCs
+    // (a step's copy overlaps the previous step's compute), the device outputs,
+    // a copy stream and the events ordering them.  Made by the first call.
+    struct HostIO {
+        bool ready;
+        int next;                  // staging buffer of the next call
+        float2 *stage[2];          // [M_max][H][W] each
+        float *phase;              // [M_max][Ho][Wo]
+        float *tcoh;               // [Ho][Wo]
+        uint8_t *status;           // [Ho][Wo]
+        uint16_t *count;           // [Ho][Wo]
+        cudaStream_t copy;
+        cudaEvent_t copied[2];     // stage[b] holds the call's SLCs
+        cudaEvent_t released[2];   // the last step reading stage[b] has run
+    } io;
 };
 
 namespace {
@@ -574,6 +589,19 @@ static void state_free(plk_state *st) {
     cudaFree(st->count);
     cudaFree(st->C);
     cudaFree(st->phase_all);
+    if (st->io.ready) {
+        cudaStreamSynchronize(st->io.copy);
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(st->io.stage[b]);
+            cudaEventDestroy(st->io.copied[b]);
+            cudaEventDestroy(st->io.released[b]);
+        }
+        cudaFree(st->io.phase);
+        cudaFree(st->io.tcoh);
+        cudaFree(st->io.status);
+        cudaFree(st->io.count);
+        cudaStreamDestroy(st->io.copy);
+    }
     delete st;
 }
 
@@ -840,6 +868,73 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     }
     st->n_eff = n_eff;
     st->steps += 1;
+    return PLK_OK;
+}
+
+plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
+                                   const plk_params *params, float *phase, float *tcoh, uint8_t *status,
+                                   uint16_t *shp_count) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_ministack_step_host: null ctx");
+    if (!st || !new_slc || M < 1 || M > st->M_max || st->K_used + M < 2)
+        return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: bad argument");
+    if (st->device != ctx->device) return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: state on another device");
+    const long long npix = (long long)st->H * st->W;
+    const long long nout = (long long)(st->H / st->win.sy) * (st->W / st->win.sx);
+    if (nout > 0 && (!phase || !tcoh || !status)) return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: null output");
+    DeviceGuard dg(ctx->device);
+    auto &io = st->io;
+    if (!io.ready) {
+        memset(&io, 0, sizeof(io));
+        const size_t nb = (size_t)st->M_max * npix * sizeof(float2), no = (size_t)(nout > 0 ? nout : 1);
+        bool ok = cudaMalloc(&io.stage[0], nb) == cudaSuccess && cudaMalloc(&io.stage[1], nb) == cudaSuccess &&
+                  cudaMalloc(&io.phase, no * st->M_max * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&io.tcoh, no * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&io.status, no) == cudaSuccess && cudaMalloc(&io.count, no * sizeof(uint16_t)) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&io.copy, cudaStreamNonBlocking) == cudaSuccess;
+        for (int b = 0; ok && b < 2; ++b)
+            ok = cudaEventCreateWithFlags(&io.copied[b], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&io.released[b], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            for (int b = 0; b < 2; ++b) {
+                cudaFree(io.stage[b]);
+                if (io.copied[b]) cudaEventDestroy(io.copied[b]);
+                if (io.released[b]) cudaEventDestroy(io.released[b]);
+            }
+            cudaFree(io.phase);
+            cudaFree(io.tcoh);
+            cudaFree(io.status);
+            cudaFree(io.count);
+            if (io.copy) cudaStreamDestroy(io.copy);
+            memset(&io, 0, sizeof(io));
+            cudaGetLastError();
+            return fail(ctx, PLK_ENOMEM, "plk_ministack_step_host: cannot allocate %zu bytes of staging", 2 * nb);
+        }
+        io.ready = true;
+    }
+    const int b = io.next;
+    io.next ^= 1;
+    // Copy stream: wait until the step that last read stage[b] has run, then copy.
+    cudaError_t e = cudaStreamWaitEvent(io.copy, io.released[b], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(io.stage[b], new_slc, (size_t)M * npix * sizeof(float2), cudaMemcpyHostToDevice, io.copy);
+    if (e == cudaSuccess) e = cudaEventRecord(io.copied[b], io.copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, io.copied[b], 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step_host: staging copy");
+    plk_status ps = plk_ministack_step(ctx, st, reinterpret_cast<const plk_c64 *>(io.stage[b]), M, params, io.phase,
+                                       io.tcoh, io.status, shp_count ? io.count : nullptr);
+    if (ps != PLK_OK) return ps;
+    e = cudaEventRecord(io.released[b], ctx->stream);
+    if (e == cudaSuccess && nout > 0) {
+        e = cudaMemcpyAsync(phase, io.phase, (size_t)M * nout * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tcoh, io.tcoh, (size_t)nout * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(status, io.status, (size_t)nout, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && shp_count)
+            e = cudaMemcpyAsync(shp_count, io.count, (size_t)nout * sizeof(uint16_t), cudaMemcpyDeviceToHost,
+                                ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step_host: output copy");
     return PLK_OK;
 }
 

@@ -86,6 +86,7 @@ _SIGS = {
     "plk_state_save": [_P, _P, ctypes.c_char_p],
     "plk_state_load": [_P, ctypes.c_char_p, _I, ctypes.POINTER(_P)],
     "plk_ministack_step": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
+    "plk_ministack_step_host": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_state_reset": [_P],
     "plk_profile_enable": [_P, _I],
     "plk_profile_collect": [_P, ctypes.POINTER(_I)],
@@ -515,6 +516,35 @@ class State:
         _check(lib().plk_ministack_step(self.ctx.h, self.h, _ptr(new_slc), M, ctypes.byref(p), _ptr(out["phase"]),
                                         _ptr(out["tcoh"]), _ptr(out["status"]), _ptr(out.get("count"))),
                self.ctx.h)
+        return out
+
+    def step_host(self, new_slc: torch.Tensor, params: Params | None = None, out: dict | None = None,
+                  want_count: bool = False) -> dict:
+        """One step from host memory (plk_ministack_step_host): new_slc a CPU
+        complex64 tensor [M, H, W] (pinned, so that its copy overlaps the
+        previous step's compute), outputs written to CPU tensors.  Asynchronous:
+        call ctx.sync() before reading the outputs or reusing new_slc."""
+        if new_slc.device.type != "cpu" or new_slc.dtype != torch.complex64 or not new_slc.is_contiguous():
+            raise TypeError("new_slc: expected a contiguous CPU complex64 tensor")
+        M = new_slc.shape[0]
+        if tuple(new_slc.shape[1:]) != (self.H, self.W):
+            raise ValueError("new_slc: wrong image size")
+        if out is None:
+            pin = torch.cuda.is_available()
+            out = {
+                "phase": torch.empty((M, self.Ho, self.Wo), dtype=torch.float32, pin_memory=pin),
+                "tcoh": torch.empty((self.Ho, self.Wo), dtype=torch.float32, pin_memory=pin),
+                "status": torch.empty((self.Ho, self.Wo), dtype=torch.uint8, pin_memory=pin),
+                "count": torch.empty((self.Ho, self.Wo), dtype=torch.int16, pin_memory=pin) if want_count else None,
+            }
+        for key in ("phase", "tcoh", "status", "count"):
+            t = out.get(key)
+            if t is not None and (t.device.type != "cpu" or not t.is_contiguous()):
+                raise TypeError(f"{key}: expected a contiguous CPU tensor")
+        p = params if params is not None else default_params()
+        _check(lib().plk_ministack_step_host(self.ctx.h, self.h, ctypes.c_void_p(new_slc.data_ptr()), M,
+                                             ctypes.byref(p), _ptr(out["phase"]), _ptr(out["tcoh"]),
+                                             _ptr(out["status"]), _ptr(out.get("count"))), self.ctx.h)
         return out
 
     def close(self):

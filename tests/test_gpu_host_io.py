@@ -1,0 +1,69 @@
+"""plk_ministack_step_host: the step with host-memory inputs and outputs and
+double-buffered staging.  A chain of calls issued back to back (each call's
+copy overlapping the previous call's compute) must give exactly the outputs
+and compressed SLCs of the same chain through plk_ministack_step on device
+buffers; pageable host memory works too."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_12051_gb300 import synth
+from parity_util import to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plk():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2511_12051_gb300 import build, plk as _plk
+    build.build()
+    return _plk
+
+
+@pytest.fixture(scope="module")
+def ctx(plk):
+    return plk.Context("cuda:0")
+
+
+def same(a, b):
+    return torch.equal(torch.nan_to_num(a.float(), nan=-9.0), torch.nan_to_num(b.float(), nan=-9.0))
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_chain_equals_device_chain(plk, ctx, pinned):
+    spec = synth.config_spec(3, scale=0.05, seed=5)        # 60 dates of 102 x 205, four mini-stacks of 15
+    z = synth.generate(spec)
+    win, M = (5, 11, 1, 1), 15
+    H, W = z.shape[1:]
+    slices = synth.ministack_slices(60, M)
+    dev = plk.State(ctx, H, W, win, K_max=3, M_max=M)
+    ref = []
+    for sl in slices:
+        o = dev.step(z[sl].contiguous().cuda())
+        ref.append({k: v.clone() for k, v in o.items() if v is not None})
+    ref_kappa = to_np(dev.kappa(dev.info()["K_used"] - 1)).copy()
+    hst = plk.State(ctx, H, W, win, K_max=3, M_max=M)
+    ins = [z[sl].contiguous().pin_memory() if pinned else z[sl].contiguous() for sl in slices]
+    outs = [hst.step_host(x, want_count=True) for x in ins]   # no sync in between
+    ctx.sync()
+    for r, o in zip(ref, outs):
+        for key in ("phase", "tcoh", "status"):
+            assert same(o[key], r[key].cpu()), key
+        assert torch.equal(o["count"], r["count"].cpu())
+    assert np.array_equal(to_np(hst.kappa(hst.info()["K_used"] - 1)), ref_kappa)
+    assert hst.info() == dev.info()
+    dev.close()
+    hst.close()
+
+
+def test_host_step_rejects_bad_inputs(plk, ctx):
+    st = plk.State(ctx, 16, 24, (3, 5, 1, 1), K_max=1, M_max=4)
+    with pytest.raises(TypeError):
+        st.step_host(torch.zeros((4, 16, 24), dtype=torch.complex64, device="cuda"))
+    with pytest.raises(ValueError):
+        st.step_host(torch.zeros((4, 16, 25), dtype=torch.complex64))
+    with pytest.raises(plk.PlkError):
+        st.step_host(torch.zeros((5, 16, 24), dtype=torch.complex64))      # M > M_max
+    st.close()
