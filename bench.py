@@ -363,10 +363,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--rows", type=int, default=H_FULL, help="image rows (smaller cases for profiling only)")
     ap.add_argument("--cols", type=int, default=W_FULL, help="image columns (smaller cases for profiling only)")
-    ap.add_argument("--cov-precision", default="fp32", choices=["fp32", "bf16"],
+    ap.add_argument("--cov-precision", default="fp32", choices=["fp32", "bf16", "fp16"],
                     help="coherence arithmetic of the timed step (fp32: the plain path)")
     ap.add_argument("--no-modes", action="store_true",
-                    help="skip timing the bfloat16-coherence and PS-regridding modes beside it")
+                    help="skip timing the reduced-precision, PS, gamma_s and L1-inversion modes beside it")
     ap.add_argument("--ps-da-max", type=float, default=0.0,
                     help="PS threshold on the amplitude dispersion in the timed step (0: no PS regridding)")
     ap.add_argument("--workload", default="burst", choices=["burst", "batch", "adjoint"],
@@ -403,7 +403,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     ctx = plk.Context(dev, stream)
     st = plk.State(ctx, spec.H, spec.W, WINDOW, K_max=6, M_max=N_DATES)
-    prec = plk.COV_BF16 if args.cov_precision == "bf16" else plk.COV_FP32
+    prec = {"fp32": plk.COV_FP32, "bf16": plk.COV_BF16, "fp16": plk.COV_FP16}[args.cov_precision]
     params = plk.default_params(cov_precision=prec, ps_da_max=args.ps_da_max)
     with torch.cuda.stream(stream):
         out = st.step(z, params)  # allocates the output tensors once
@@ -603,6 +603,9 @@ def main():
         modes = {}
         modes["bf16_covariance"] = time_mode(plk.default_params(cov_precision=plk.COV_BF16))
         modes["bf16_covariance"]["accuracy"] = ("measured against the FP64 oracle by tests/test_gpu_bf16.py "
+                                                "(linked-phase p50/p99/max)")
+        modes["fp16_covariance"] = time_mode(plk.default_params(cov_precision=plk.COV_FP16))
+        modes["fp16_covariance"]["accuracy"] = ("measured against the FP64 oracle by tests/test_gpu_fp16.py "
                                                 "(linked-phase p50/p99/max)")
         modes["ps_regrid"] = time_mode(plk.default_params(ps_da_max=PS_DA_MAX))
         modes["ps_regrid"]["ps_da_max"] = PS_DA_MAX

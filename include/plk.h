@@ -84,9 +84,11 @@ typedef struct plk_params {
                           eigengap seen by the iteration) exceeds err_max are
                           re-solved in double precision; default 0.1 (the bound
                           is loose: measured errors sit 1e3-1e4 below it) */
-    int32_t cov_precision; /* coherence arithmetic (S3): PLK_COV_FP32 (default) or
+    int32_t cov_precision; /* coherence arithmetic (S3): PLK_COV_FP32 (default),
                               PLK_COV_BF16 (samples rounded to bfloat16, sums in
-                              single precision on the tensor cores; N <= 32) */
+                              single precision on the tensor cores; N <= 32) or
+                              PLK_COV_FP16 (the same with half-precision samples,
+                              scaled by a power of two per tile; N <= 32) */
     int32_t ref_scheme;    /* mini-stack reference scheme of plk_ministack_step:
                               PLK_REF_FIRST (default) or PLK_REF_LAST_REAL */
     float ps_da_max;       /* plk_ministack_step: when > 0, output cells whose
@@ -115,6 +117,7 @@ typedef struct plk_params {
 /* Coherence precision modes (plk_params.cov_precision, plk_estimate_covariance). */
 #define PLK_COV_FP32 0
 #define PLK_COV_BF16 1
+#define PLK_COV_FP16 2
 
 typedef struct plk_ctx plk_ctx;
 typedef struct plk_state plk_state;
@@ -197,7 +200,10 @@ plk_status plk_shp_select(plk_ctx *ctx, const float *sum_pow, int n_eff, int H, 
  * at i*N - i*(i-1)/2 + (k - i).  precision PLK_COV_FP32: single-precision
  * products and sums; PLK_COV_BF16: the samples are rounded to bfloat16 (round
  * to nearest even) and the products summed in single precision on the tensor
- * cores, N <= 32 (EUNSUPPORTED beyond). */
+ * cores, N <= 32 (EUNSUPPORTED beyond); PLK_COV_FP16: the same with the
+ * samples of each output tile's region scaled by one power of two (its largest
+ * component into [2^14, 2^15), cancelled exactly by the normalisation) and
+ * rounded to half precision (round to nearest even), N <= 32. */
 plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W,
                                    plk_window win, const uint64_t *mask, int precision,
                                    plk_c64 *C_packed);

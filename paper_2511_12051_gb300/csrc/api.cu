@@ -135,7 +135,7 @@ plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::E
     else plk_default_params(&p);
     if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
         !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0) ||
-        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16) ||
+        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16 && p.cov_precision != PLK_COV_FP16) ||
         (p.ref_scheme != PLK_REF_FIRST && p.ref_scheme != PLK_REF_LAST_REAL) ||
         !(p.ps_da_max >= 0.f && p.ps_da_max < 1e30f))
         return fail(ctx, PLK_EINVAL, "bad plk_params");
@@ -357,10 +357,10 @@ plk_status plk_estimate_covariance(plk_ctx *ctx, const plk_c64 *slc, int N, int 
                                    const uint64_t *mask, int precision, plk_c64 *C_packed) {
     if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_estimate_covariance: null ctx");
     if (!slc || N < 2 || N > PLK_MAX_N || H < 1 || W < 1 || !window_ok(win) ||
-        (precision != PLK_COV_FP32 && precision != PLK_COV_BF16))
+        (precision != PLK_COV_FP32 && precision != PLK_COV_BF16 && precision != PLK_COV_FP16))
         return fail(ctx, PLK_EINVAL, "plk_estimate_covariance: bad argument");
-    if (precision == PLK_COV_BF16 && N > 32)
-        return fail(ctx, PLK_EUNSUPPORTED, "plk_estimate_covariance: bfloat16 mode needs N <= 32 (N=%d)", N);
+    if (precision != PLK_COV_FP32 && N > 32)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_estimate_covariance: tensor-core modes need N <= 32 (N=%d)", N);
     if ((long long)(H / win.sy) * (W / win.sx) > 0 && (!mask || !C_packed))
         return fail(ctx, PLK_EINVAL, "plk_estimate_covariance: null pointer");
     if (!aligned(slc, 8) || !aligned(mask, 8) || !aligned(C_packed, 8))
@@ -781,8 +781,8 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     float ps_da_max = 0.f;
     plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision, &ref_scheme, &ps_da_max);
     if (ps != PLK_OK) return ps;
-    if (cov_precision == PLK_COV_BF16 && st->K_used + M > 32)
-        return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: bfloat16 coherence needs N <= 32");
+    if (cov_precision != PLK_COV_FP32 && st->K_used + M > 32)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: tensor-core coherence modes need N <= 32");
     DeviceGuard dg(ctx->device);
     const Geom g = plk::make_geom(st->H, st->W, st->win);
     const long long npix = (long long)st->H * st->W, nout = (long long)g.Ho * g.Wo;

@@ -107,8 +107,8 @@ plk_status plk_batch_create(plk_ctx *ctx, const plk_stack_desc *stacks, int n_st
             return fail(ctx, PLK_EINVAL, "plk_batch_create: stack %d: null output", i);
         if (!aligned(d.slc, 8) || !aligned(d.phase, 4) || !aligned(d.tcoh, 4))
             return fail(ctx, PLK_EINVAL, "plk_batch_create: stack %d: misaligned pointer", i);
-        if (cov_precision == PLK_COV_BF16 && d.N > 32)
-            return fail(ctx, PLK_EUNSUPPORTED, "plk_batch_create: stack %d: bfloat16 coherence needs N <= 32", i);
+        if (cov_precision != PLK_COV_FP32 && d.N > 32)
+            return fail(ctx, PLK_EUNSUPPORTED, "plk_batch_create: stack %d: tensor-core coherence modes need N <= 32", i);
     }
     DeviceGuard dg(ctx->device);
     plk_batch *b = new (std::nothrow) plk_batch;

@@ -622,6 +622,7 @@ static cudaError_t run_cov(const Planes &z, int n, const Geom &g, const uint64_t
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                               cudaStream_t s, int precision, const Schedule *sch) {
     if (precision == 1) return launch_covariance_bf16(z, n, g, mask, C, s);
+    if (precision == 2) return launch_covariance_fp16(z, n, g, mask, C, s);
     // 3 x 3 block grid (5 pixels per warp) up to N = 18; 5 x 5 (2 per warp) beyond
     // (blocks of 5 or more dates: 4-date blocks on a 5 x 5 grid collide in banks).
     // Kept in step with block_shape().

@@ -1,6 +1,13 @@
 // S3 in reduced precision: SHP-windowed sample coherence (Sec. II-A, eq.
-// (sample-coherence)) with the samples rounded to bfloat16 and the sums
-// accumulated in single precision on the tensor cores (mma.sync m16n8k16).
+// (sample-coherence)) with the samples rounded to bfloat16 or to half
+// precision and the sums accumulated in single precision on the tensor cores
+// (mma.sync m16n8k16).
+//
+// Half precision has three more significand bits than bfloat16 but a narrow
+// exponent range, so each tile's samples are first scaled by one power of two
+// that puts the tile's largest component in [2^14, 2^15): exact, and exactly
+// cancelled by the normalisation C_ik = S_ik / sqrt(S_ii S_kk), since every
+// window of the tile's output pixels lies inside the tile's region.
 //
 // Per output pixel the sum S = sum_q m(q) z(q) z(q)^H is a small dense
 // contraction over its looks.  With x = Re z, y = Im z (vectors over dates)
@@ -23,11 +30,12 @@
 // position.
 //
 // The records are filled with ordinary coalesced loads (16 in flight per
-// thread), rounded to bfloat16 (round to nearest even) and stored with 16-byte
+// thread), rounded to 16 bits (round to nearest even) and stored with 16-byte
 // stores; for N <= 16 two CTAs share an SM, one loading while the other runs
 // its tensor work.  (A variant staging the region through TMA boxes, one CTA
 // per SM, and one interleaving two pixels per warp were both slower.)
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -59,36 +67,55 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t addr) {
                  : "r"(addr));
 }
 
-// D += A B, m16n8k16, bfloat16 inputs, single-precision accumulators.
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// D += A B, m16n8k16, bfloat16 (F16 = false) or half-precision (F16 = true)
+// inputs, single-precision accumulators.
+template <bool F16>
+__device__ __forceinline__ void mma_16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    if constexpr (F16) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%0, %1, %2, %3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    } else {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%0, %1, %2, %3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
 }
 
-// (x, y) packed as (low, high) bfloat16 -> (y, -x).
+// (x, y) packed as (low, high) 16-bit values -> (y, -x) (the sign is bit 15
+// of each half in both formats).
 __device__ __forceinline__ uint32_t swap_neg(uint32_t v) { return __byte_perm(v, 0, 0x1032) ^ 0x80000000u; }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+template <bool F16>
+__device__ __forceinline__ uint32_t pack_16(float lo, float hi) {
     uint32_t u;
-    memcpy(&u, &h, 4);
+    if constexpr (F16) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        memcpy(&u, &h, 4);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        memcpy(&u, &h, 4);
+    }
     return u;
 }
 
-// Store 8 samples of one date group of one pixel as two bfloat16 units.
-__device__ __forceinline__ void store_group(unsigned char *rec, int q, const float2 (&v)[8]) {
+// Store 8 samples (times the tile's scale) of one date group of one pixel as
+// two units of 16-bit values.
+template <bool F16>
+__device__ __forceinline__ void store_group(unsigned char *rec, int q, const float2 (&v)[8], float sc) {
     uint4 ux, uy;
-    ux.x = pack_bf16(v[0].x, v[1].x);
-    ux.y = pack_bf16(v[2].x, v[3].x);
-    ux.z = pack_bf16(v[4].x, v[5].x);
-    ux.w = pack_bf16(v[6].x, v[7].x);
-    uy.x = pack_bf16(v[0].y, v[1].y);
-    uy.y = pack_bf16(v[2].y, v[3].y);
-    uy.z = pack_bf16(v[4].y, v[5].y);
-    uy.w = pack_bf16(v[6].y, v[7].y);
+    ux.x = pack_16<F16>(v[0].x * sc, v[1].x * sc);
+    ux.y = pack_16<F16>(v[2].x * sc, v[3].x * sc);
+    ux.z = pack_16<F16>(v[4].x * sc, v[5].x * sc);
+    ux.w = pack_16<F16>(v[6].x * sc, v[7].x * sc);
+    uy.x = pack_16<F16>(v[0].y * sc, v[1].y * sc);
+    uy.y = pack_16<F16>(v[2].y * sc, v[3].y * sc);
+    uy.z = pack_16<F16>(v[4].y * sc, v[5].y * sc);
+    uy.w = pack_16<F16>(v[6].y * sc, v[7].y * sc);
     uint4 *u = reinterpret_cast<uint4 *>(rec);
     u[2 * q] = ux;
     u[2 * q + 1] = uy;
@@ -162,7 +189,7 @@ struct MmaLane {
 
 // Tensor-core sums, normalisation and packed stores for the tile's pixels,
 // one pixel per warp at a time.
-template <int NT>
+template <int NT, bool F16>
 __device__ __forceinline__ void mma_tile(const MmaLane<NT> &ln, const MmaSmem<NT> &s, const MmaLayout &lay, int n,
                                          const Geom &g, const uint64_t *__restrict__ mask, float2 *__restrict__ C,
                                          int ty0, int tx0) {
@@ -227,10 +254,10 @@ __device__ __forceinline__ void mma_tile(const MmaLane<NT> &ln, const MmaSmem<NT
 #pragma unroll
                 for (int b = 0; b < MT; ++b) {
                     // column tiles of 8 dates: 16b + 0-7 and 16b + 8-15
-                    mma_bf16(dre[a][2 * b], f[a], f[b][0], f[b][2]);
-                    mma_bf16(dre[a][2 * b + 1], f[a], f[b][1], f[b][3]);
-                    mma_bf16(dim[a][2 * b], as, f[b][0], f[b][2]);
-                    mma_bf16(dim[a][2 * b + 1], as, f[b][1], f[b][3]);
+                    mma_16<F16>(dre[a][2 * b], f[a], f[b][0], f[b][2]);
+                    mma_16<F16>(dre[a][2 * b + 1], f[a], f[b][1], f[b][3]);
+                    mma_16<F16>(dim[a][2 * b], as, f[b][0], f[b][2]);
+                    mma_16<F16>(dim[a][2 * b + 1], as, f[b][1], f[b][3]);
                 }
             }
             if (step + 1 < nsteps) {
@@ -296,7 +323,7 @@ __device__ __forceinline__ void mma_tile(const MmaLane<NT> &ln, const MmaSmem<NT
 }  // namespace
 
 // Ordinary loads.  NT = 16 or 32 dates per pixel record (N <= NT).
-template <int NT>
+template <int NT, bool F16>
 __global__ void __launch_bounds__(256, NT == 16 ? 2 : 1) k_cov_mma(const __grid_constant__ Planes z, int n,
                                                                    const Geom g, const uint64_t *__restrict__ mask,
                                                                    float2 *__restrict__ C, const MmaLayout lay,
@@ -321,43 +348,66 @@ __global__ void __launch_bounds__(256, NT == 16 ? 2 : 1) k_cov_mma(const __grid_
     }
     const int adv = 2 * blockDim.x, adv_y = adv / lay.RX, adv_x = adv - adv_y * lay.RX;
 
+    __shared__ unsigned tile_max;  // largest |component| of the region, as float bits (half precision only)
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty0 = (int)(t % tilesY) * lay.TY;
         const int tx0 = (int)(t / tilesY) * lay.TX;
         const int y0 = ty0 * g.sy + g.sy / 2 - g.hy;
         const int x0 = tx0 * g.sx + g.sx / 2 - g.hx;
+        if (F16 && threadIdx.x == 0) tile_max = 0u;
         __syncthreads();  // previous tile's reads done (and the tables written)
-        int q[2] = {cq[0], cq[1]}, ry[2] = {cy[0], cy[1]}, rx[2] = {cx[0], cx[1]};
-        for (int idx0 = threadIdx.x; idx0 < ntask; idx0 += adv) {
-            float2 v[2][8];
+        // One pass over this thread's tasks of the region: fn(h, v, ry, rx, q)
+        // gets each task's 8 samples (zero outside the image and past n).
+        auto for_tasks = [&](auto &&fn) {
+            int q[2] = {cq[0], cq[1]}, ry[2] = {cy[0], cy[1]}, rx[2] = {cx[0], cx[1]};
+            for (int idx0 = threadIdx.x; idx0 < ntask; idx0 += adv) {
+                float2 v[2][8];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int y = y0 + ry[h], x = x0 + rx[h];
-                const bool inside = idx0 + h * (int)blockDim.x < ntask && y >= 0 && y < g.H && x >= 0 && x < g.W;
-                const long long off = inside ? (long long)y * g.W + x : 0;
+                for (int h = 0; h < 2; ++h) {
+                    const int y = y0 + ry[h], x = x0 + rx[h];
+                    const bool inside =
+                        idx0 + h * (int)blockDim.x < ntask && y >= 0 && y < g.H && x >= 0 && x < g.W;
+                    const long long off = inside ? (long long)y * g.W + x : 0;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int d = q[h] * 8 + u;
-                    v[h][u] = (inside && d < n) ? __ldg(z.p[d] + off) : make_float2(0.f, 0.f);
+                    for (int u = 0; u < 8; ++u) {
+                        const int d = q[h] * 8 + u;
+                        v[h][u] = (inside && d < n) ? __ldg(z.p[d] + off) : make_float2(0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (idx0 + h * (int)blockDim.x < ntask) fn(v[h], ry[h], rx[h], q[h]);
+                    rx[h] += adv_x;
+                    ry[h] += adv_y;
+                    if (rx[h] >= lay.RX) {
+                        rx[h] -= lay.RX;
+                        ++ry[h];
+                    }
+                    while (ry[h] >= lay.RY) {
+                        ry[h] -= lay.RY;
+                        ++q[h];
+                    }
                 }
             }
+        };
+        float sc = 1.f;
+        if constexpr (F16) {
+            float m = 0.f;
+            for_tasks([&](const float2 (&v)[8], int, int, int) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (idx0 + h * (int)blockDim.x < ntask) store_group(s.rec + (size_t)(ry[h] * lay.RX + rx[h]) * PXB, q[h], v[h]);
-                rx[h] += adv_x;
-                ry[h] += adv_y;
-                if (rx[h] >= lay.RX) {
-                    rx[h] -= lay.RX;
-                    ++ry[h];
-                }
-                while (ry[h] >= lay.RY) {
-                    ry[h] -= lay.RY;
-                    ++q[h];
-                }
-            }
+                for (int u = 0; u < 8; ++u) m = fmaxf(m, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
+            });
+            atomicMax(&tile_max, __float_as_uint(m));  // non-negative floats order as their bits
+            __syncthreads();
+            const float mx = __uint_as_float(tile_max);
+            // 2^(14 - e) for mx in [2^e, 2^(e+1)): the largest component lands in [2^14, 2^15)
+            if (mx > 0.f && mx < __int_as_float(0x7f800000)) sc = ldexpf(1.f, max(-126, min(127, 14 - ilogbf(mx))));
         }
+        for_tasks([&](const float2 (&v)[8], int ry, int rx, int q) {
+            store_group<F16>(s.rec + (size_t)(ry * lay.RX + rx) * PXB, q, v, sc);
+        });
         __syncthreads();
-        mma_tile<NT>(ln, s, lay, n, g, mask, C, ty0, tx0);
+        mma_tile<NT, F16>(ln, s, lay, n, g, mask, C, ty0, tx0);
     }
 }
 
@@ -392,7 +442,7 @@ static MmaLayout choose_mma_layout(int NT, const Geom &g, size_t budget) {
     return best;
 }
 
-template <int NT>
+template <int NT, bool F16>
 static cudaError_t run_cov_mma_plain(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                                      cudaStream_t s) {
     // Two CTAs per SM share its shared memory for NT = 16.
@@ -400,25 +450,32 @@ static cudaError_t run_cov_mma_plain(const Planes &z, int n, const Geom &g, cons
     const MmaLayout lay = choose_mma_layout(NT, g, budget);
     if (lay.TY == 0) return cudaErrorInvalidConfiguration;
     cudaError_t e =
-        cudaFuncSetAttribute(k_cov_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem);
+        cudaFuncSetAttribute(k_cov_mma<NT, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cov_mma<NT>, 256, lay.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cov_mma<NT, F16>, 256, lay.smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int tilesY = (g.Ho + lay.TY - 1) / lay.TY;
     const long long ntiles = (long long)tilesY * ((g.Wo + lay.TX - 1) / lay.TX);
     if (ntiles == 0) return cudaSuccess;
     const long long grid = std::min<long long>(ntiles, (long long)per_sm * device_sm_count());
-    k_cov_mma<NT><<<(unsigned)grid, 256, lay.smem, s>>>(z, n, g, mask, C, lay, ntiles, tilesY);
+    k_cov_mma<NT, F16><<<(unsigned)grid, 256, lay.smem, s>>>(z, n, g, mask, C, lay, ntiles, tilesY);
     return cudaGetLastError();
 }
 
 cudaError_t launch_covariance_bf16(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                                    cudaStream_t s) {
     if (n > 32) return cudaErrorInvalidValue;
-    if (n <= 16) return run_cov_mma_plain<16>(z, n, g, mask, C, s);
-    return run_cov_mma_plain<32>(z, n, g, mask, C, s);
+    if (n <= 16) return run_cov_mma_plain<16, false>(z, n, g, mask, C, s);
+    return run_cov_mma_plain<32, false>(z, n, g, mask, C, s);
+}
+
+cudaError_t launch_covariance_fp16(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
+                                   cudaStream_t s) {
+    if (n > 32) return cudaErrorInvalidValue;
+    if (n <= 16) return run_cov_mma_plain<16, true>(z, n, g, mask, C, s);
+    return run_cov_mma_plain<32, true>(z, n, g, mask, C, s);
 }
 
 }  // namespace plk

@@ -72,8 +72,11 @@ cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint6
 // Up to max candidate single-precision coherence tiles {TY, TX} for (n, g),
 // best heuristic score first; returns the count.
 int covariance_tile_candidates(int n, const Geom &g, int (*tiles)[2], int max);
-// precision 1: bfloat16 samples, tensor-core sums (n <= 32).
+// precision 1: bfloat16 samples, tensor-core sums (n <= 32); precision 2:
+// half-precision samples scaled by a power of two per tile, same sums.
 cudaError_t launch_covariance_bf16(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
+                                   cudaStream_t s);
+cudaError_t launch_covariance_fp16(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                                    cudaStream_t s);
 struct Prof;
 // Where the double-precision re-solve recomputes a pixel's coherence from:

@@ -52,6 +52,7 @@ class StackDesc(ctypes.Structure):
 
 COV_FP32 = 0  # PLK_COV_FP32
 COV_BF16 = 1  # PLK_COV_BF16
+COV_FP16 = 2  # PLK_COV_FP16
 REF_FIRST = 0  # PLK_REF_FIRST
 REF_LAST_REAL = 1  # PLK_REF_LAST_REAL
 
