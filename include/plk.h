@@ -372,6 +372,20 @@ plk_status plk_phase_link_backward(plk_ctx *ctx, const plk_c64 *slc, int N, int 
                                    const float *dphase, void *workspace, size_t workspace_bytes,
                                    plk_c64 *dslc);
 
+/* Phase uncertainty through the adjoint: the first-order standard deviation
+ * of every linked phase when white circular Gaussian noise of variance sigma2
+ * (E|n|^2 = sigma2) is added to every SLC sample, SHP masks frozen.  For
+ * pixel p and date i, with g(q) = H z(q) the adjoint's gradient of phihat_i(p)
+ * over the pixel's masked window, Var phihat_i = (sigma2 / 2) sum_q |g(q)|^2 =
+ * (sigma2 / 2) tr(H^H H S), S = sum_q m(q) z(q) z(q)^H (the pixel's
+ * unnormalised sample covariance); one adjoint solve per date, no window
+ * scatter.  phase_std [N][Ho][Wo] float: 0 at ref_idx, NaN without data.
+ * Workspace as plk_backward_workspace_size.  Not in the paper (it applies the
+ * adjoint to uncertainty propagation).  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+plk_status plk_phase_uncertainty(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W, plk_window win,
+                                 const uint64_t *mask, int ref_idx, const plk_params *params, float sigma2,
+                                 void *workspace, size_t workspace_bytes, float *phase_std);
+
 /* ------------------------------------------------ batches of stacks */
 
 /* One independent stack of a batch: its SLCs and where its outputs go (all

@@ -82,6 +82,171 @@ __global__ void __launch_bounds__(256) k_adj_sdiag(const __grid_constant__ Plane
     }
 }
 
+// Per-pixel state of the adjoint that does not depend on the phase weights:
+// the eigenvector v (this lane's entry, and every lane's), the coherence row,
+// the G^-1 row, the inverted deflated matrix (A - lambda I + c v v^H)^-1 (row),
+// 1/sqrt(S_kk) for every k and this row's S_rr.
+template <int NP>
+struct AdjPixelState {
+    cpx<float> v, crow[NP], vv[NP], mrow[NP];
+    float gi[NP], rs[NP], sr, rsr;
+    bool evd, live;
+};
+
+template <int NP>
+__device__ __forceinline__ void adj_prepare(AdjPixelState<NP> &S, const AdjRow<NP> &ld, const float *__restrict__ Sd,
+                                            long long p, int r, int n, int ref, const EmiParams &q,
+                                            cpx<float> *cbuf, unsigned gmask, int glane0) {
+    float *rbuf = reinterpret_cast<float *>(cbuf);
+    S.live = r < n;
+    const PixelResult res = emi_solve<NP, float>(ld, r, n, ref, q, cbuf, gmask, glane0, false);
+    S.evd = res.evd;
+    S.v = S.live ? res.v : mk<float>(0.f, 0.f);
+    // A row (C, or G^-1 o C) and G^-1 row.
+    cpx<float> a[NP];
+    load_crow<NP, float>(S.crow, ld, r, n);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        float m = mag_t(norm2(S.crow[k]));
+        if (q.beta != 0.f) m = (1.f - q.beta) * m + ((k == r) ? q.beta : 0.f);
+        S.gi[k] = m;
+    }
+    if (!S.evd) gj_invert<NP, float, float, true>(S.gi, rbuf, r, n, gmask, 0.f);
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+        a[k] = S.evd ? S.crow[k] : mk<float>(S.gi[k] * S.crow[k].x, S.gi[k] * S.crow[k].y);
+    // lambda = v^H A v (the eigenvalue the perturbation is about)
+    const cpx<float> av = group_matvec<NP, float>(a, S.v, cbuf, r, gmask);
+    const float lam = group_sum<NP, float>(S.live ? (S.v.x * av.x + S.v.y * av.y) : 0.f, gmask);
+    // every lane's v
+    cbuf[r] = S.v;
+    __syncwarp(gmask);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) S.vv[k] = cbuf[k];
+    __syncwarp(gmask);
+    // (A - lambda I + c v v^H)^-1  (c keeps the deflated matrix well scaled)
+    const float cdef = fmaxf(1.f, fabsf(lam));
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        S.mrow[k] = a[k] + cdef * (S.v * conj(S.vv[k]));
+        if (k == r && S.live) S.mrow[k].x -= lam;
+    }
+    gj_invert<NP, float, cpx<float>, false>(S.mrow, cbuf, r, n, gmask, 0.f);
+    // 1 / sqrt(S_kk), every k
+    S.sr = S.live ? __ldg(Sd + p * n + r) : 0.f;
+    S.rsr = S.sr > 0.f ? rsqrtf(S.sr) : 0.f;
+    rbuf[r] = S.rsr;
+    __syncwarp(gmask);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) S.rs[k] = rbuf[k];
+    __syncwarp(gmask);
+}
+
+// Row r of H = GS + GS^H for the phase weight wr of this lane's date (the
+// weight of the reference date is unused: its phase is 0).
+template <int NP>
+__device__ __forceinline__ void adj_h_row(const AdjPixelState<NP> &S, float wr, int r, int n, int ref, float beta,
+                                          cpx<float> *cbuf, cpx<float> *cmat, unsigned gmask, cpx<float> (&h)[NP]) {
+    float *fmat = reinterpret_cast<float *>(cmat);
+    // Gradient on v (gauge-free), projected orthogonal to v.
+    const float wsum = group_sum<NP, float>(S.live && r != ref ? wr : 0.f, gmask);
+    const float m2 = norm2(S.v);
+    const float coef = (r == ref) ? -wsum : wr;
+    cpx<float> gv = (S.live && m2 > 0.f) ? (coef / m2) * mk<float>(-S.v.y, S.v.x) : mk<float>(0.f, 0.f);
+    {
+        const cpx<float> t = conj(S.v) * gv;
+        const float sx = group_sum<NP, float>(t.x, gmask), sy = group_sum<NP, float>(t.y, gmask);
+        gv = gv - S.v * mk<float>(sx, sy);
+    }
+    // u = (A - lambda I + c v v^H)^-1 g_v  (u orthogonal to v)
+    const cpx<float> u = group_matvec<NP, float>(S.mrow, gv, cbuf, r, gmask);
+
+    // GA = -u v^H (row r), then GC (off the diagonal).
+    cpx<float> gc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) gc[k] = mk<float>(0.f, 0.f) - u * conj(S.vv[k]);  // GA for now
+    if (!S.evd) {
+        float R[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) R[k] = gc[k].x * S.crow[k].x + gc[k].y * S.crow[k].y;  // Re(conj(GA) C)
+        // T = G^-1 R (row r): sum_j gi[j] R_j.
+        publish<NP, float>(R, fmat, r, gmask);
+        float T[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) T[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+#pragma unroll
+            for (int k = 0; k < NP; ++k) T[k] += S.gi[j] * fmat[j * NP + k];
+        // GG = -T G^-1 (row r): -sum_j T[j] Ginv_j.
+        publish<NP, float>(S.gi, fmat, r, gmask);
+        float GG[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) GG[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+#pragma unroll
+            for (int k = 0; k < NP; ++k) GG[k] -= T[j] * fmat[j * NP + k];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float cm2 = norm2(S.crow[k]);
+            const cpx<float> ph = cm2 > 0.f ? rsqrtf(cm2) * S.crow[k] : mk<float>(0.f, 0.f);
+            gc[k] = S.gi[k] * gc[k] + ((1.f - beta) * GG[k]) * ph;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+        if (k == r || k >= n || !S.live) gc[k] = mk<float>(0.f, 0.f);
+
+    // C -> S.
+    float P[NP];
+    float rowsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        P[k] = gc[k].x * S.crow[k].x + gc[k].y * S.crow[k].y;
+        rowsum += P[k];
+    }
+    publish<NP, float>(P, fmat, r, gmask);
+    float colsum = 0.f;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) colsum += fmat[i * NP + r];
+    cpx<float> gs[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) gs[k] = (S.rsr * S.rs[k]) * gc[k];
+    if (S.live && S.sr > 0.f) gs[r] = mk<float>(-(rowsum + colsum) / (2.f * S.sr), 0.f);
+
+    // H = GS + GS^H (row r)
+    publish<NP, cpx<float>>(gs, cmat, r, gmask);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) h[k] = gs[k] + conj(cmat[k * NP + r]);
+    __syncwarp(gmask);
+}
+
+// Coherence row r of pixel p, unit diagonal, into the lane's row cache.
+template <int NP>
+__device__ __forceinline__ void adj_load_row(cpx<float> *myrow, const float2 *__restrict__ Cpix, int r, int n) {
+    const bool live = r < n;
+    const int base_r = r * n - r * (r - 1) / 2 - r;
+    int idx_col = r;
+    cpx<float> v[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        v[k] = mk<float>((!live && k == r) ? 1.f : 0.f, 0.f);
+        if (live && k < n) {
+            if (k >= r) {
+                const float2 c = __ldg(Cpix + base_r + k);
+                v[k] = mk<float>(c.x, c.y);
+            } else {
+                const float2 c = __ldg(Cpix + idx_col);
+                v[k] = mk<float>(c.x, -c.y);
+                idx_col += n - k - 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) myrow[k] = v[k];
+}
+
 // Per output pixel: H_p from the coherence C (packed), the diagonal sums and
 // the phase weights w [n][npx].  Pixels without data get H_p = 0.
 template <int NP>
@@ -273,6 +438,89 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_pixel(const float2 *__re
     }
 }
 
+// First-order phase uncertainty: white circular noise of variance sigma2 on
+// every SLC sample, E|n|^2 = sigma2, propagated through the linked phases.
+// With g(q) = H_p z(q) the gradient of phihat_i(p) over the pixel's masked
+// window, Var phihat_i = (sigma2 / 2) sum_q |g(q)|^2 = (sigma2 / 2) tr(H^H H S),
+// S = sum_q m(q) z(q) z(q)^H, S_jk = C_jk sqrt(S_jj S_kk).  H is Hermitian, so
+// tr(H^H H S) = sum_k <row k of H, row k of H S>: each lane's own rows.
+// One pass per date with the weight e_i; the reference date has 0.
+template <int NP>
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adj_uncert(const float2 *__restrict__ C,
+                                                               const float *__restrict__ Sd, int n, long long npx,
+                                                               int ref, const EmiParams prm, float sigma2,
+                                                               float *__restrict__ sd_out) {
+    constexpr int G = 32 / NP;
+    constexpr int kRowPitch = NP + 2;
+    constexpr int kGrpBuf = 2 * NP + 2;
+    __shared__ __align__(16) cpx<float> sbuf[kAdjWarps][G * kGrpBuf];
+    __shared__ __align__(16) cpx<float> rowcache[kAdjWarps * 32 * kRowPitch];
+    __shared__ __align__(16) cpx<float> mats[kAdjWarps][32 * NP];
+    __shared__ __align__(16) cpx<float> smats[kAdjWarps][32 * NP];  // S of the group's pixel
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / NP, r = lane - grp * NP;
+    const int glane0 = grp * NP;
+    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const long long nt = ntri(n);
+    const long long step = (long long)gridDim.x * kAdjWarps * G;
+    cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
+    cpx<float> *cbuf = &sbuf[warp][grp * kGrpBuf];
+    float *rbuf = reinterpret_cast<float *>(cbuf);
+    cpx<float> *cmat = &mats[warp][grp * NP * NP];
+    cpx<float> *smat = &smats[warp][grp * NP * NP];
+    EmiParams q = prm;
+    q.fp64_resolve = 0;
+    const float qnan = __int_as_float(0x7fc00000);
+
+    for (long long base = ((long long)blockIdx.x * kAdjWarps + warp) * G; base < npx; base += step) {
+        const long long p = base + grp;
+        const bool valid = p < npx;
+        const float2 *Cpix = C + (valid ? p : 0) * nt;
+        const bool live = r < n;
+        bool nan = false;
+        if (valid && live) nan = isnan(__ldg(Cpix + packed_index(n, r, r)).x);
+        nan = __any_sync(gmask, nan);
+        if (!valid) continue;
+        if (nan) {
+            if (live) sd_out[(long long)r * npx + p] = qnan;
+            continue;
+        }
+        adj_load_row<NP>(myrow, Cpix, r, n);
+        __syncwarp(gmask);
+        AdjPixelState<NP> S;
+        adj_prepare<NP>(S, AdjRow<NP>{myrow}, Sd, p, r, n, ref, q, cbuf, gmask, glane0);
+        // S rows (unnormalised): S_rk = C_rk sqrt(S_rr S_kk)
+        {
+            // sqrt(S_rr S_kk) = sqrt(S_rr) / rs_k, rs_k = 1 / sqrt(S_kk) (0 where S_kk = 0)
+            const float sq_r = sqrtf(S.sr);
+            cpx<float> srow[NP];
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                srow[k] = (live && k < n && S.rs[k] > 0.f) ? (sq_r / S.rs[k]) * S.crow[k] : mk<float>(0.f, 0.f);
+            publish<NP, cpx<float>>(srow, smat, r, gmask);
+        }
+        float sd_mine = 0.f;  // this lane's date
+        for (int i = 0; i < n; ++i) {
+            if (i == ref) continue;  // uniform across the group
+            cpx<float> h[NP];
+            adj_h_row<NP>(S, (r == i) ? 1.f : 0.f, r, n, ref, q.beta, cbuf, cmat, gmask, h);
+            // row r of M = H S, then <row r of H, row r of M>
+            float tr = 0.f;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                cpx<float> m = mk<float>(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) m = cfma(h[j], smat[j * NP + k], m);
+                tr += h[k].x * m.x + h[k].y * m.y;  // Re(conj(h_k) m_k)
+            }
+            tr = group_sum<NP, float>(live ? tr : 0.f, gmask);
+            if (r == i) sd_mine = sqrtf(fmaxf(0.5f * sigma2 * tr, 0.f));
+        }
+        if (live) sd_out[(long long)r * npx + p] = sd_mine;  // 0 at the reference date
+        __syncwarp(gmask);
+    }
+}
+
 // Per (input pixel q, date i): g_i(q) = sum over the output pixels p whose
 // window holds q, with q's mask bit set, of sum_k H_p,ik z_k(q).  NT >= n.
 // The date index runs fastest across threads: a warp covers one or two
@@ -449,6 +697,17 @@ static cudaError_t run_adj_pixel(const float2 *C, const float *Sd, int n, long l
     return cudaGetLastError();
 }
 
+template <int NP>
+static cudaError_t run_adj_uncert(const float2 *C, const float *Sd, int n, long long npx, int ref,
+                                  const EmiParams &prm, float sigma2, float *out, cudaStream_t s) {
+    constexpr int G = 32 / NP;
+    long long blocks = ((npx + G - 1) / G + kAdjWarps - 1) / kAdjWarps;
+    const long long cap = (long long)device_sm_count() * 16;
+    blocks = std::max<long long>(1, std::min(blocks, cap));
+    k_adj_uncert<NP><<<(unsigned)blocks, kAdjWarps * 32, 0, s>>>(C, Sd, n, npx, ref, prm, sigma2, out);
+    return cudaGetLastError();
+}
+
 // Workspace layout: C [npx][ntri], H [npx][ntri], Sd [npx][n] (256-byte aligned parts).
 size_t adjoint_workspace_bytes(int n, const Geom &g) {
     const long long npx = (long long)g.Ho * g.Wo;
@@ -509,6 +768,26 @@ cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t
     e = cudaGetLastError();
     if (prof) prof->end(s);
     return e;
+}
+
+// First-order phase standard deviations (k_adj_uncert) over the workspace of
+// the adjoint: the coherence and the diagonal sums are recomputed there.
+cudaError_t launch_phase_uncertainty(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
+                                     const EmiParams &prm, float sigma2, void *workspace, float *sd,
+                                     cudaStream_t s) {
+    const long long npx = (long long)g.Ho * g.Wo;
+    if (npx == 0) return cudaSuccess;
+    auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    char *ws = static_cast<char *>(workspace);
+    float2 *C = reinterpret_cast<float2 *>(ws);
+    float *Sd = reinterpret_cast<float *>(ws + 2 * a256((size_t)npx * ntri(n) * sizeof(float2)));
+    cudaError_t e = launch_covariance(z, n, g, mask, C, s);
+    if (e != cudaSuccess) return e;
+    k_adj_sdiag<<<adj_grid(npx * n), 256, 0, s>>>(z, n, g, mask, Sd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n <= 8) return run_adj_uncert<8>(C, Sd, n, npx, ref, prm, sigma2, sd, s);
+    if (n <= 16) return run_adj_uncert<16>(C, Sd, n, npx, ref, prm, sigma2, sd, s);
+    return run_adj_uncert<32>(C, Sd, n, npx, ref, prm, sigma2, sd, s);
 }
 
 }  // namespace plk
