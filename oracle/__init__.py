@@ -240,3 +240,4 @@ def ps_compress(z: np.ndarray, first_real: int, sum_pow: np.ndarray, sum_amp: np
 from .chain import OracleChain, ministack  # noqa: E402,F401
 from .similarity import disk_offsets, nearest3_pairs, phase_similarity  # noqa: E402,F401
 from .inversion import incidence, l1_invert, soft_threshold  # noqa: E402,F401
+from .weights import mask_weights, weighted_coherence, window_samples  # noqa: E402,F401
