@@ -288,7 +288,8 @@ def run_adjoint(args, rank: int, world: int, local: int):
     """Adjoint workload: N=20 x 1024x1024 (cfg0-type coherence and ramp), 11x5
     window, stride 1, masks frozen; forward = coherence + EMI (single-precision
     solve), backward = plk_phase_link_backward of sum(w * phase), w ~ U(-1, 1);
-    beside it, plk_phase_uncertainty (one adjoint solve per date and pixel)."""
+    beside it, plk_phase_uncertainty (one adjoint solve per date and pixel) and
+    plk_shp_weight_gradient (dL/dw over every window sample)."""
     import torch
     from paper_2511_12051_gb300 import build, synth, plk
     from paper_2511_12051_gb300 import dist as pdist
@@ -311,6 +312,7 @@ def run_adjoint(args, rank: int, world: int, local: int):
         w = torch.rand(out["phase"].shape, device=dev, generator=g) * 2 - 1
         dz = ctx.phase_link_backward(z, win, mask, 0, w, prm)
         sd = ctx.phase_uncertainty(z, win, mask, 0, 0.01, prm)
+        dwt = ctx.shp_weight_gradient(z, win, mask, 0, w, prm)
     torch.cuda.synchronize(dev)
 
     def fwd():
@@ -335,7 +337,10 @@ def run_adjoint(args, rank: int, world: int, local: int):
     def unc():
         ctx.phase_uncertainty(z, win, mask, 0, 0.01, prm, out=sd)
 
-    ms_f, ms_b, ms_u = timed(fwd), timed(bwd), timed(unc)
+    def wgrad():
+        ctx.shp_weight_gradient(z, win, mask, 0, w, prm, out=dwt)
+
+    ms_f, ms_b, ms_u, ms_w = timed(fwd), timed(bwd), timed(unc), timed(wgrad)
     ctx.profile(True)
     with torch.cuda.stream(stream):
         for _ in range(2):
@@ -354,7 +359,8 @@ def run_adjoint(args, rank: int, world: int, local: int):
             "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
             "backward_stages_ms": stages,
             "forward_px_per_s": npx * world / (ms_f / 1e3),
-            "uncertainty_ms": ms_u, "uncertainty_px_per_s": npx * world / (ms_u / 1e3)}), flush=True)
+            "uncertainty_ms": ms_u, "uncertainty_px_per_s": npx * world / (ms_u / 1e3),
+            "weight_gradient_ms": ms_w}), flush=True)
     return 0
 
 

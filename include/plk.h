@@ -372,6 +372,21 @@ plk_status plk_phase_link_backward(plk_ctx *ctx, const plk_c64 *slc, int N, int 
                                    const float *dphase, void *workspace, size_t workspace_bytes,
                                    plk_c64 *dslc);
 
+/* Gradient of L = sum(dphase * phase) with respect to real per-sample window
+ * weights, the SHP mask read as weights w_b in the sample covariance
+ * S = sum_b w_b z(q_b) z(q_b)^H (Sec. II-A, eq. (sample-coherence) with a
+ * weighted sum), evaluated at w = mask: dL/dw_b = (1/2) z(q_b)^H H_p z(q_b),
+ * H_p the adjoint's matrix of pixel p (see plk_phase_link_backward).  Samples
+ * outside the mask get the derivative of adding them with a small weight;
+ * samples outside the image and pixels without data get 0.  Scaling every
+ * weight of a pixel leaves its coherence unchanged, so the sum over its
+ * masked samples is 0.  dweight [Ho][Wo][wy*wx] float, b = (dy + wy/2) * wx +
+ * (dx + wx/2) as in the mask bits.  Workspace as plk_backward_workspace_size.
+ * Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+plk_status plk_shp_weight_gradient(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W, plk_window win,
+                                   const uint64_t *mask, int ref_idx, const plk_params *params,
+                                   const float *dphase, void *workspace, size_t workspace_bytes, float *dweight);
+
 /* Phase uncertainty through the adjoint: the first-order standard deviation
  * of every linked phase when white circular Gaussian noise of variance sigma2
  * (E|n|^2 = sigma2) is added to every SLC sample, SHP masks frozen.  For

@@ -573,6 +573,40 @@ plk_status plk_phase_link_backward(plk_ctx *ctx, const plk_c64 *slc, int N, int 
     return PLK_OK;
 }
 
+plk_status plk_shp_weight_gradient(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W, plk_window win,
+                                   const uint64_t *mask, int ref_idx, const plk_params *params,
+                                   const float *dphase, void *workspace, size_t workspace_bytes, float *dweight) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_shp_weight_gradient: null ctx");
+    if (!slc || N < 2 || N > PLK_MAX_N || H < 1 || W < 1 || !window_ok(win) || ref_idx < 0 || ref_idx >= N)
+        return fail(ctx, PLK_EINVAL, "plk_shp_weight_gradient: bad argument");
+    const plk::Geom g = plk::make_geom(H, W, win);
+    const long long npx = (long long)g.Ho * g.Wo;
+    if (npx > 0 && (!mask || !dphase || !workspace || !dweight))
+        return fail(ctx, PLK_EINVAL, "plk_shp_weight_gradient: null pointer");
+    const size_t need = plk::adjoint_workspace_bytes(N, g);
+    if (workspace_bytes < need)
+        return fail(ctx, PLK_EINVAL, "plk_shp_weight_gradient: workspace of %zu bytes, %zu needed", workspace_bytes,
+                    need);
+    if (!aligned(slc, 8) || !aligned(mask, 8) || !aligned(dphase, 4) || !aligned(dweight, 4) ||
+        !aligned(workspace, 256))
+        return fail(ctx, PLK_EINVAL, "plk_shp_weight_gradient: misaligned pointer");
+    plk::EmiParams prm;
+    double alpha;
+    plk_status ps = resolve_params(ctx, params, &prm, &alpha);
+    if (ps != PLK_OK) return ps;
+    DeviceGuard dg(ctx->device);
+    Planes z{};
+    for (int t = 0; t < N; ++t) z.p[t] = reinterpret_cast<const float2 *>(slc) + (long long)t * H * W;
+    ctx->prof.begin("shp_weight_gradient", ctx->stream);
+    cudaError_t e = plk::launch_weight_gradient(z, N, g, mask, ref_idx, prm, dphase, workspace, dweight,
+                                                ctx->stream);
+    ctx->prof.end(ctx->stream);
+    if (e == cudaErrorInvalidConfiguration)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_shp_weight_gradient: window with N=%d exceeds shared memory", N);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_shp_weight_gradient");
+    return PLK_OK;
+}
+
 plk_status plk_phase_uncertainty(plk_ctx *ctx, const plk_c64 *slc, int N, int H, int W, plk_window win,
                                  const uint64_t *mask, int ref_idx, const plk_params *params, float sigma2,
                                  void *workspace, size_t workspace_bytes, float *phase_std) {

@@ -175,18 +175,22 @@ __device__ __forceinline__ void adj_h_row(const AdjPixelState<NP> &S, float wr, 
 #pragma unroll
         for (int k = 0; k < NP; ++k) T[k] = 0.f;
 #pragma unroll
-        for (int j = 0; j < NP; ++j)
+        for (int j = 0; j < NP; ++j) {
+            if (j >= n) break;  // rows past n are zero
 #pragma unroll
             for (int k = 0; k < NP; ++k) T[k] += S.gi[j] * fmat[j * NP + k];
+        }
         // GG = -T G^-1 (row r): -sum_j T[j] Ginv_j.
         publish<NP, float>(S.gi, fmat, r, gmask);
         float GG[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) GG[k] = 0.f;
 #pragma unroll
-        for (int j = 0; j < NP; ++j)
+        for (int j = 0; j < NP; ++j) {
+            if (j >= n) break;  // T_j = 0 past n
 #pragma unroll
             for (int k = 0; k < NP; ++k) GG[k] -= T[j] * fmat[j * NP + k];
+        }
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             const float cm2 = norm2(S.crow[k]);
@@ -508,9 +512,13 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_uncert(const float2 *__r
             float tr = 0.f;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
+                if (k >= n) break;  // S and H are zero past n
                 cpx<float> m = mk<float>(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < NP; ++j) m = cfma(h[j], smat[j * NP + k], m);
+                for (int j = 0; j < NP; ++j) {
+                    if (j >= n) break;
+                    m = cfma(h[j], smat[j * NP + k], m);
+                }
                 tr += h[k].x * m.x + h[k].y * m.y;  // Re(conj(h_k) m_k)
             }
             tr = group_sum<NP, float>(live ? tr : 0.f, gmask);
@@ -571,6 +579,56 @@ __global__ void __launch_bounds__(256) k_adj_gather(const __grid_constant__ Plan
             }
         }
         grad[(long long)i * npix + qi] = make_float2(acc.x, acc.y);
+    }
+}
+
+// Gradient of L with respect to real per-sample window weights (the SHP mask
+// read as weights w_b in S = sum_b w_b z(q_b) z(q_b)^H, evaluated at w = mask):
+// dL/dw_b = Re sum_jk conj(GS_jk) z_j conj(z_k) = (1/2) z^H H_p z, z = z(q_b);
+// 0 for window samples outside the image and for pixels without data (H_p = 0).
+// One thread per (output pixel, window sample), samples fastest: a warp spans
+// one or two pixels, so its loads of H_p are broadcasts.  NT >= n.
+template <int NT>
+__global__ void __launch_bounds__(256) k_adj_wgrad(const __grid_constant__ Planes z, int n, const Geom g,
+                                                   const float2 *__restrict__ H, float *__restrict__ dw) {
+    const long long npx = (long long)g.Ho * g.Wo;
+    const int nb = g.wy * g.wx;
+    const long long total = npx * nb;
+    const long long nt = ntri(n);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long o = t / nb;
+        const int b = (int)(t - o * nb);
+        const int oy = (int)(o / g.Wo), ox = (int)(o - (long long)oy * g.Wo);
+        const int by = b / g.wx, bx = b - by * g.wx;
+        const int y = oy * g.sy + g.sy / 2 - g.hy + by, x = ox * g.sx + g.sx / 2 - g.hx + bx;
+        float acc = 0.f;
+        if (y >= 0 && y < g.H && x >= 0 && x < g.W) {
+            const long long qi = (long long)y * g.W + x;
+            cpx<float> zq[NT];
+#pragma unroll
+            for (int k = 0; k < NT; ++k) {
+                const float2 v = k < n ? __ldg(z.p[k] + qi) : make_float2(0.f, 0.f);
+                zq[k] = mk<float>(v.x, v.y);
+            }
+            // z^H H z = sum_j H_jj |z_j|^2 + 2 Re sum_{j<k} conj(z_j) H_jk z_k
+            const float2 *Hp = H + o * nt;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                if (j >= n) break;
+                const float2 *row = Hp + packed_index(n, j, j);
+                const float2 hd = __ldg(row);
+                cpx<float> s = mk<float>(0.f, 0.f);
+#pragma unroll
+                for (int k = j + 1; k < NT; ++k) {
+                    if (k >= n) break;
+                    const float2 h = __ldg(row + (k - j));
+                    s = cfma(mk<float>(h.x, h.y), zq[k], s);
+                }
+                acc += hd.x * norm2(zq[j]) + 2.f * (zq[j].x * s.x + zq[j].y * s.y);
+            }
+        }
+        dw[t] = 0.5f * acc;
     }
 }
 
@@ -715,16 +773,18 @@ size_t adjoint_workspace_bytes(int n, const Geom &g) {
     return 2 * a256((size_t)npx * ntri(n) * sizeof(float2)) + a256((size_t)npx * n * sizeof(float));
 }
 
-cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
-                           const EmiParams &prm, const float *dphase, void *workspace, float2 *grad,
-                           cudaStream_t s, Prof *prof) {
-    const long long npx = (long long)g.Ho * g.Wo, npix = (long long)g.H * g.W;
+// Recomputed coherence, diagonal sums and H_p of every output pixel into the
+// workspace; *Hout points at H.  npx > 0.
+static cudaError_t adjoint_h(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
+                             const EmiParams &prm, const float *dphase, void *workspace, cudaStream_t s, Prof *prof,
+                             float2 **Hout) {
+    const long long npx = (long long)g.Ho * g.Wo;
     auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
     char *ws = static_cast<char *>(workspace);
     float2 *C = reinterpret_cast<float2 *>(ws);
     float2 *H = reinterpret_cast<float2 *>(ws + a256((size_t)npx * ntri(n) * sizeof(float2)));
     float *Sd = reinterpret_cast<float *>(ws + 2 * a256((size_t)npx * ntri(n) * sizeof(float2)));
-    if (npx == 0) return cudaMemsetAsync(grad, 0, (size_t)npix * n * sizeof(float2), s);
+    *Hout = H;
     if (prof) prof->begin("adjoint_covariance", s);
     cudaError_t e = launch_covariance(z, n, g, mask, C, s);  // recomputed, not stored by the forward pass
     if (prof) prof->end(s);
@@ -736,6 +796,16 @@ cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t
     else if (n <= 16) e = run_adj_pixel<16>(C, Sd, n, npx, ref, prm, dphase, H, s);
     else e = run_adj_pixel<32>(C, Sd, n, npx, ref, prm, dphase, H, s);
     if (prof) prof->end(s);
+    return e;
+}
+
+cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
+                           const EmiParams &prm, const float *dphase, void *workspace, float2 *grad,
+                           cudaStream_t s, Prof *prof) {
+    const long long npx = (long long)g.Ho * g.Wo, npix = (long long)g.H * g.W;
+    if (npx == 0) return cudaMemsetAsync(grad, 0, (size_t)npix * n * sizeof(float2), s);
+    float2 *H = nullptr;
+    cudaError_t e = adjoint_h(z, n, g, mask, ref, prm, dphase, workspace, s, prof, &H);
     if (e != cudaSuccess) return e;
     if (prof) prof->begin("adjoint_gather", s);
     const size_t kBudget = 150 * 1024;
@@ -768,6 +838,23 @@ cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t
     e = cudaGetLastError();
     if (prof) prof->end(s);
     return e;
+}
+
+// Gradient of L = sum(dphase * phase) with respect to the window weights
+// [Ho][Wo][wy*wx] (k_adj_wgrad) over the workspace of the adjoint.
+cudaError_t launch_weight_gradient(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
+                                   const EmiParams &prm, const float *dphase, void *workspace, float *dw,
+                                   cudaStream_t s) {
+    const long long npx = (long long)g.Ho * g.Wo;
+    if (npx == 0) return cudaSuccess;
+    float2 *H = nullptr;
+    cudaError_t e = adjoint_h(z, n, g, mask, ref, prm, dphase, workspace, s, nullptr, &H);
+    if (e != cudaSuccess) return e;
+    const int grid = adj_grid(npx * g.wy * g.wx);
+    if (n <= 8) k_adj_wgrad<8><<<grid, 256, 0, s>>>(z, n, g, H, dw);
+    else if (n <= 16) k_adj_wgrad<16><<<grid, 256, 0, s>>>(z, n, g, H, dw);
+    else k_adj_wgrad<32><<<grid, 256, 0, s>>>(z, n, g, H, dw);
+    return cudaGetLastError();
 }
 
 // First-order phase standard deviations (k_adj_uncert) over the workspace of

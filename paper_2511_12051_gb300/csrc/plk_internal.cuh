@@ -142,6 +142,11 @@ size_t adjoint_workspace_bytes(int n, const Geom &g);
 cudaError_t launch_adjoint(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
                            const EmiParams &prm, const float *dphase, void *workspace, float2 *grad,
                            cudaStream_t s, Prof *prof = nullptr);
+// Gradient of sum(dphase * phase) with respect to real window weights at the
+// SHP mask, [Ho][Wo][wy*wx] (the adjoint's workspace).
+cudaError_t launch_weight_gradient(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,
+                                   const EmiParams &prm, const float *dphase, void *workspace, float *dw,
+                                   cudaStream_t s);
 // First-order standard deviation of the linked phases [n][Ho][Wo] under white
 // circular noise of variance sigma2 on the samples (the adjoint's workspace).
 cudaError_t launch_phase_uncertainty(const Planes &z, int n, const Geom &g, const uint64_t *mask, int ref,

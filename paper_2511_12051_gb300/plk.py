@@ -96,6 +96,8 @@ _SIGS = {
     "plk_backward_workspace_size": [_I, _I, _I, Window, ctypes.POINTER(ctypes.c_size_t)],
     "plk_phase_link_backward": [_P, _P, _I, _I, _I, Window, _P, _I, ctypes.POINTER(Params), _P, _P,
                                 ctypes.c_size_t, _P],
+    "plk_shp_weight_gradient": [_P, _P, _I, _I, _I, Window, _P, _I, ctypes.POINTER(Params), _P, _P,
+                                ctypes.c_size_t, _P],
     "plk_phase_uncertainty": [_P, _P, _I, _I, _I, Window, _P, _I, ctypes.POINTER(Params), ctypes.c_float, _P,
                               ctypes.c_size_t, _P],
     "plk_batch_create": [_P, _P, _I, Window, ctypes.POINTER(Params), ctypes.POINTER(_P)],
@@ -309,6 +311,27 @@ class Context:
         _check(lib().plk_phase_link_backward(self.h, _ptr(slc), N, H, W, w, _ptr(mask), int(ref), ctypes.byref(p),
                                              _ptr(dphase), _ptr(ws), nbytes.value, _ptr(dslc)), self.h)
         return dslc
+
+    def shp_weight_gradient(self, slc: torch.Tensor, win, mask: torch.Tensor, ref: int, dphase: torch.Tensor,
+                            params: Params | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Gradient [Ho, Wo, wy*wx] of L = sum(dphase * phase) with respect to
+        real per-sample window weights, evaluated at the SHP mask."""
+        _need(slc, torch.complex64, "slc", self.device)
+        _need(mask, torch.int64, "mask", self.device)
+        _need(dphase, torch.float32, "dphase", self.device)
+        N, H, W = slc.shape
+        w = window(win)
+        Ho, Wo = output_shape(H, W, win)
+        nbytes = ctypes.c_size_t()
+        _check(lib().plk_backward_workspace_size(N, H, W, w, ctypes.byref(nbytes)))
+        ws = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=self.device)
+        if out is None:
+            out = torch.empty((Ho, Wo, w.wy * w.wx), dtype=torch.float32, device=self.device)
+        _need(out, torch.float32, "out", self.device)
+        p = params if params is not None else default_params()
+        _check(lib().plk_shp_weight_gradient(self.h, _ptr(slc), N, H, W, w, _ptr(mask), int(ref), ctypes.byref(p),
+                                             _ptr(dphase), _ptr(ws), nbytes.value, _ptr(out)), self.h)
+        return out
 
     def phase_uncertainty(self, slc: torch.Tensor, win, mask: torch.Tensor, ref: int, sigma2: float,
                           params: Params | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
