@@ -483,6 +483,26 @@ def main():
     roof["traffic"] = per_px * npx if (per_px and args.rows == H_FULL and args.cols == W_FULL) else None
     roof["avg_launch_ms"] = dom_ms / dom_n
 
+    # Whole step against its roofline: a kernel's ideal time is the larger of its
+    # algorithmic flops at the FP32 peak and its algorithmic bytes at the HBM
+    # peak; the fraction is the sum of the ideal times over the measured step.
+    hbm_bs = peaks.get("hbm_gbs", 6800.0) * 1e9
+    plane = spec.H * spec.W
+    ntri = N_DATES * (N_DATES + 1) // 2
+    ideal = {
+        "amp_stats": (0.0, N_DATES * plane * 8 + plane * 8),
+        "shp_select": (0.0, plane * 4 + npx * 10),
+        "covariance": (flops_covariance(N_DATES, looks_total), N_DATES * plane * 8 + npx * 8 + npx * ntri * 8),
+        "phase_link_fp32": (flops_emi(N_DATES, npx), npx * ntri * 8 + npx * (4 * N_DATES + 5)),
+        "phase_link_fp64": (0.0, npx),
+        "compress": (0.0, N_DATES * plane * 8 + plane * 8),
+    }
+    t_ideal = {kk: max(f / (FP32_PEAK_TFLOPS * 1e12), b / hbm_bs) * 1e3 for kk, (f, b) in ideal.items()}
+    step_roof = {"ideal_ms": sum(t_ideal.values()), "step_ms": ms_step,
+                 "frac": sum(t_ideal.values()) / ms_step,
+                 "ideal_ms_by_kernel": t_ideal,
+                 "model": "per kernel max(algorithmic flops / FP32 peak, algorithmic bytes / HBM peak), summed"}
+
     # ------------------------------------------------------------------ e2e
     # Through the C ABI with host buffers (plk_ministack_step_host): every step
     # copies its 15 SLCs from pinned host memory and writes phases, gamma_t and
@@ -648,6 +668,7 @@ def main():
                        "l2": "inputs (8.05 GB per step) larger than L2; no flush",
                        "parallelism": f"{world} independent bursts, one per GPU"},
             "roofline": roof,
+            "step_roofline": step_roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
