@@ -524,6 +524,15 @@ def main():
         e2e_step()
         ctx.sync()
         torch.cuda.synchronize(dev)
+        # The host link's rate at this moment (it is shared with the other GPUs
+        # of the node): one plain pinned-host -> device copy of the same bytes.
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            l0.record(stream)
+            z.copy_(zh, non_blocking=True)
+            l1.record(stream)
+        torch.cuda.synchronize(dev)
+        link_gbs = bi / (l0.elapsed_time(l1) / 1e3) / 1e9
         pdist.barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -536,7 +545,8 @@ def main():
         torch.cuda.synchronize(dev)
         ms_e2e = pdist.max_over_ranks(f0.elapsed_time(f1), dev)
         e2e = {"value": npx * world * ne / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_e2e / ne}
+               "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_e2e / ne,
+               "h2d_link_gbs": link_gbs, "input_copy_bound_ms": bi / (link_gbs * 1e9) * 1e3}
         del zh, oh
 
     # ------------------------- other modes of the same step, timed beside it
