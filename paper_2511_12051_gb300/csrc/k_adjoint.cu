@@ -82,71 +82,83 @@ __global__ void __launch_bounds__(256) k_adj_sdiag(const __grid_constant__ Plane
     }
 }
 
-// Per-pixel state of the adjoint that does not depend on the phase weights:
-// the eigenvector v (this lane's entry, and every lane's), the coherence row,
-// the G^-1 row, the inverted deflated matrix (A - lambda I + c v v^H)^-1 (row),
-// 1/sqrt(S_kk) for every k and this row's S_rr.
+// Per-pixel state of the uncertainty kernel that does not depend on the date:
+// in registers, this lane's eigenvector entry and its row of the inverted
+// deflated matrix (A - lambda I + c v v^H)^-1; in the group's shared memory
+// (UncShared), the coherence row (the lane's row cache), every lane's v, every
+// 1/sqrt(S_kk) and G^-1.  Keeping the group-uniform vectors and the rows that
+// are only read out of the register file leaves the per-date products room.
 template <int NP>
 struct AdjPixelState {
-    cpx<float> v, crow[NP], vv[NP], mrow[NP];
-    float gi[NP], rs[NP], sr, rsr;
+    cpx<float> v, mrow[NP];
+    float sr, rsr;
     bool evd, live;
 };
 
+// Group views of the shared buffers: row r of C (myrow, padded), v and
+// 1/sqrt(S_kk) of every lane, G^-1 [NP][NP].
 template <int NP>
-__device__ __forceinline__ void adj_prepare(AdjPixelState<NP> &S, const AdjRow<NP> &ld, const float *__restrict__ Sd,
+struct UncShared {
+    const cpx<float> *myrow;
+    cpx<float> *vg;
+    float *rsg;
+    float *ginv;
+};
+
+template <int NP>
+__device__ __forceinline__ void adj_prepare(AdjPixelState<NP> &S, const UncShared<NP> &sh, const float *__restrict__ Sd,
                                             long long p, int r, int n, int ref, const EmiParams &q,
                                             cpx<float> *cbuf, unsigned gmask, int glane0) {
     float *rbuf = reinterpret_cast<float *>(cbuf);
+    const AdjRow<NP> ld{sh.myrow};
     S.live = r < n;
     const PixelResult res = emi_solve<NP, float>(ld, r, n, ref, q, cbuf, gmask, glane0, false);
     S.evd = res.evd;
     S.v = S.live ? res.v : mk<float>(0.f, 0.f);
-    // A row (C, or G^-1 o C) and G^-1 row.
-    cpx<float> a[NP];
-    load_crow<NP, float>(S.crow, ld, r, n);
+    // G^-1 row, published to the group's matrix.
+    {
+        float gi[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float m = mag_t(norm2(sh.myrow[k]));
+            if (q.beta != 0.f) m = (1.f - q.beta) * m + ((k == r) ? q.beta : 0.f);
+            gi[k] = m;
+        }
+        if (!S.evd) gj_invert<NP, float, float, true>(gi, rbuf, r, n, gmask, 0.f);
+        publish<NP, float>(gi, sh.ginv, r, gmask);
+    }
+    // A row (C, or G^-1 o C) into mrow; lambda = v^H A v.
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        float m = mag_t(norm2(S.crow[k]));
-        if (q.beta != 0.f) m = (1.f - q.beta) * m + ((k == r) ? q.beta : 0.f);
-        S.gi[k] = m;
+        const cpx<float> c = sh.myrow[k];
+        const float gk = sh.ginv[r * NP + k];
+        S.mrow[k] = S.evd ? c : mk<float>(gk * c.x, gk * c.y);
     }
-    if (!S.evd) gj_invert<NP, float, float, true>(S.gi, rbuf, r, n, gmask, 0.f);
-#pragma unroll
-    for (int k = 0; k < NP; ++k)
-        a[k] = S.evd ? S.crow[k] : mk<float>(S.gi[k] * S.crow[k].x, S.gi[k] * S.crow[k].y);
-    // lambda = v^H A v (the eigenvalue the perturbation is about)
-    const cpx<float> av = group_matvec<NP, float>(a, S.v, cbuf, r, gmask);
+    const cpx<float> av = group_matvec<NP, float>(S.mrow, S.v, cbuf, r, gmask);
     const float lam = group_sum<NP, float>(S.live ? (S.v.x * av.x + S.v.y * av.y) : 0.f, gmask);
-    // every lane's v
-    cbuf[r] = S.v;
-    __syncwarp(gmask);
-#pragma unroll
-    for (int k = 0; k < NP; ++k) S.vv[k] = cbuf[k];
+    sh.vg[r] = S.v;
     __syncwarp(gmask);
     // (A - lambda I + c v v^H)^-1  (c keeps the deflated matrix well scaled)
     const float cdef = fmaxf(1.f, fabsf(lam));
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        S.mrow[k] = a[k] + cdef * (S.v * conj(S.vv[k]));
+        S.mrow[k] = S.mrow[k] + cdef * (S.v * conj(sh.vg[k]));
         if (k == r && S.live) S.mrow[k].x -= lam;
     }
     gj_invert<NP, float, cpx<float>, false>(S.mrow, cbuf, r, n, gmask, 0.f);
-    // 1 / sqrt(S_kk), every k
     S.sr = S.live ? __ldg(Sd + p * n + r) : 0.f;
     S.rsr = S.sr > 0.f ? rsqrtf(S.sr) : 0.f;
-    rbuf[r] = S.rsr;
-    __syncwarp(gmask);
-#pragma unroll
-    for (int k = 0; k < NP; ++k) S.rs[k] = rbuf[k];
+    sh.rsg[r] = S.rsr;
     __syncwarp(gmask);
 }
 
 // Row r of H = GS + GS^H for the phase weight wr of this lane's date (the
-// weight of the reference date is unused: its phase is 0).
+// weight of the reference date is unused: its phase is 0).  Products over the
+// date index stop at n (rows and columns past n are zero).
 template <int NP>
-__device__ __forceinline__ void adj_h_row(const AdjPixelState<NP> &S, float wr, int r, int n, int ref, float beta,
-                                          cpx<float> *cbuf, cpx<float> *cmat, unsigned gmask, cpx<float> (&h)[NP]) {
+__device__ __forceinline__ void adj_h_row(const AdjPixelState<NP> &S, const UncShared<NP> &sh, float wr, int r, int n,
+                                          int ref, float beta, cpx<float> *cbuf, cpx<float> *cmat, unsigned gmask,
+                                          cpx<float> (&h)[NP]) {
     float *fmat = reinterpret_cast<float *>(cmat);
     // Gradient on v (gauge-free), projected orthogonal to v.
     const float wsum = group_sum<NP, float>(S.live && r != ref ? wr : 0.f, gmask);
@@ -161,68 +173,75 @@ __device__ __forceinline__ void adj_h_row(const AdjPixelState<NP> &S, float wr, 
     // u = (A - lambda I + c v v^H)^-1 g_v  (u orthogonal to v)
     const cpx<float> u = group_matvec<NP, float>(S.mrow, gv, cbuf, r, gmask);
 
-    // GA = -u v^H (row r), then GC (off the diagonal).
-    cpx<float> gc[NP];
+    // GA = -u v^H (row r), then GC (off the diagonal); h holds GC.
 #pragma unroll
-    for (int k = 0; k < NP; ++k) gc[k] = mk<float>(0.f, 0.f) - u * conj(S.vv[k]);  // GA for now
+    for (int k = 0; k < NP; ++k) h[k] = mk<float>(0.f, 0.f) - u * conj(sh.vg[k]);
     if (!S.evd) {
-        float R[NP];
-#pragma unroll
-        for (int k = 0; k < NP; ++k) R[k] = gc[k].x * S.crow[k].x + gc[k].y * S.crow[k].y;  // Re(conj(GA) C)
-        // T = G^-1 R (row r): sum_j gi[j] R_j.
-        publish<NP, float>(R, fmat, r, gmask);
         float T[NP];
+        {
+            float R[NP];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const cpx<float> c = sh.myrow[k];
+                R[k] = h[k].x * c.x + h[k].y * c.y;  // Re(conj(GA) C)
+            }
+            publish<NP, float>(R, fmat, r, gmask);
+        }
+        // T = G^-1 R (row r)
 #pragma unroll
         for (int k = 0; k < NP; ++k) T[k] = 0.f;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            if (j >= n) break;  // rows past n are zero
+            if (j >= n) break;
+            const float gj = sh.ginv[r * NP + j];
 #pragma unroll
-            for (int k = 0; k < NP; ++k) T[k] += S.gi[j] * fmat[j * NP + k];
+            for (int k = 0; k < NP; ++k) T[k] += gj * fmat[j * NP + k];
         }
-        // GG = -T G^-1 (row r): -sum_j T[j] Ginv_j.
-        publish<NP, float>(S.gi, fmat, r, gmask);
+        // GG = -T G^-1 (row r)
         float GG[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) GG[k] = 0.f;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            if (j >= n) break;  // T_j = 0 past n
+            if (j >= n) break;
 #pragma unroll
-            for (int k = 0; k < NP; ++k) GG[k] -= T[j] * fmat[j * NP + k];
+            for (int k = 0; k < NP; ++k) GG[k] -= T[j] * sh.ginv[j * NP + k];
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            const float cm2 = norm2(S.crow[k]);
-            const cpx<float> ph = cm2 > 0.f ? rsqrtf(cm2) * S.crow[k] : mk<float>(0.f, 0.f);
-            gc[k] = S.gi[k] * gc[k] + ((1.f - beta) * GG[k]) * ph;
+            const cpx<float> c = sh.myrow[k];
+            const float cm2 = norm2(c);
+            const cpx<float> ph = cm2 > 0.f ? rsqrtf(cm2) * c : mk<float>(0.f, 0.f);
+            h[k] = sh.ginv[r * NP + k] * h[k] + ((1.f - beta) * GG[k]) * ph;
         }
     }
 #pragma unroll
     for (int k = 0; k < NP; ++k)
-        if (k == r || k >= n || !S.live) gc[k] = mk<float>(0.f, 0.f);
+        if (k == r || k >= n || !S.live) h[k] = mk<float>(0.f, 0.f);
 
     // C -> S.
-    float P[NP];
-    float rowsum = 0.f;
+    {
+        float P[NP];
+        float rowsum = 0.f;
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        P[k] = gc[k].x * S.crow[k].x + gc[k].y * S.crow[k].y;
-        rowsum += P[k];
+        for (int k = 0; k < NP; ++k) {
+            const cpx<float> c = sh.myrow[k];
+            P[k] = h[k].x * c.x + h[k].y * c.y;
+            rowsum += P[k];
+        }
+        publish<NP, float>(P, fmat, r, gmask);
+        float colsum = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) colsum += fmat[i * NP + r];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) h[k] = (S.rsr * sh.rsg[k]) * h[k];
+        if (S.live && S.sr > 0.f) h[r] = mk<float>(-(rowsum + colsum) / (2.f * S.sr), 0.f);
     }
-    publish<NP, float>(P, fmat, r, gmask);
-    float colsum = 0.f;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) colsum += fmat[i * NP + r];
-    cpx<float> gs[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) gs[k] = (S.rsr * S.rs[k]) * gc[k];
-    if (S.live && S.sr > 0.f) gs[r] = mk<float>(-(rowsum + colsum) / (2.f * S.sr), 0.f);
 
     // H = GS + GS^H (row r)
-    publish<NP, cpx<float>>(gs, cmat, r, gmask);
+    publish<NP, cpx<float>>(h, cmat, r, gmask);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) h[k] = gs[k] + conj(cmat[k * NP + r]);
+    for (int k = 0; k < NP; ++k) h[k] = h[k] + conj(cmat[k * NP + r]);
     __syncwarp(gmask);
 }
 
@@ -448,35 +467,41 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_pixel(const float2 *__re
 // window, Var phihat_i = (sigma2 / 2) sum_q |g(q)|^2 = (sigma2 / 2) tr(H^H H S),
 // S = sum_q m(q) z(q) z(q)^H, S_jk = C_jk sqrt(S_jj S_kk).  H is Hermitian, so
 // tr(H^H H S) = sum_k <row k of H, row k of H S>: each lane's own rows.
-// One pass per date with the weight e_i; the reference date has 0.
+// One pass per date with the weight e_i; the reference date has 0.  One warp
+// a CTA (the shared buffers of a 32-lane group take 30 KB).
+constexpr int kUncWarps = 1;
+
 template <int NP>
-__global__ void __launch_bounds__(kAdjWarps * 32) k_adj_uncert(const float2 *__restrict__ C,
+__global__ void __launch_bounds__(kUncWarps * 32) k_adj_uncert(const float2 *__restrict__ C,
                                                                const float *__restrict__ Sd, int n, long long npx,
                                                                int ref, const EmiParams prm, float sigma2,
                                                                float *__restrict__ sd_out) {
     constexpr int G = 32 / NP;
     constexpr int kRowPitch = NP + 2;
     constexpr int kGrpBuf = 2 * NP + 2;
-    __shared__ __align__(16) cpx<float> sbuf[kAdjWarps][G * kGrpBuf];
-    __shared__ __align__(16) cpx<float> rowcache[kAdjWarps * 32 * kRowPitch];
-    __shared__ __align__(16) cpx<float> mats[kAdjWarps][32 * NP];
-    __shared__ __align__(16) cpx<float> smats[kAdjWarps][32 * NP];  // S of the group's pixel
+    __shared__ __align__(16) cpx<float> sbuf[kUncWarps][G * kGrpBuf];
+    __shared__ __align__(16) cpx<float> rowcache[kUncWarps * 32 * kRowPitch];
+    __shared__ __align__(16) cpx<float> mats[kUncWarps][32 * NP];
+    __shared__ __align__(16) cpx<float> smats[kUncWarps][32 * NP];  // S of the group's pixel
+    __shared__ __align__(16) float ginvs[kUncWarps][32 * NP];       // G^-1 of the group's pixel
+    __shared__ __align__(16) cpx<float> vs[kUncWarps][32];
+    __shared__ __align__(16) float rss[kUncWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / NP, r = lane - grp * NP;
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
-    const long long step = (long long)gridDim.x * kAdjWarps * G;
+    const long long step = (long long)gridDim.x * kUncWarps * G;
     cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
     cpx<float> *cbuf = &sbuf[warp][grp * kGrpBuf];
-    float *rbuf = reinterpret_cast<float *>(cbuf);
     cpx<float> *cmat = &mats[warp][grp * NP * NP];
     cpx<float> *smat = &smats[warp][grp * NP * NP];
+    const UncShared<NP> sh{myrow, &vs[warp][glane0], &rss[warp][glane0], &ginvs[warp][grp * NP * NP]};
     EmiParams q = prm;
     q.fp64_resolve = 0;
     const float qnan = __int_as_float(0x7fc00000);
 
-    for (long long base = ((long long)blockIdx.x * kAdjWarps + warp) * G; base < npx; base += step) {
+    for (long long base = ((long long)blockIdx.x * kUncWarps + warp) * G; base < npx; base += step) {
         const long long p = base + grp;
         const bool valid = p < npx;
         const float2 *Cpix = C + (valid ? p : 0) * nt;
@@ -492,22 +517,24 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_uncert(const float2 *__r
         adj_load_row<NP>(myrow, Cpix, r, n);
         __syncwarp(gmask);
         AdjPixelState<NP> S;
-        adj_prepare<NP>(S, AdjRow<NP>{myrow}, Sd, p, r, n, ref, q, cbuf, gmask, glane0);
+        adj_prepare<NP>(S, sh, Sd, p, r, n, ref, q, cbuf, gmask, glane0);
         // S rows (unnormalised): S_rk = C_rk sqrt(S_rr S_kk)
         {
             // sqrt(S_rr S_kk) = sqrt(S_rr) / rs_k, rs_k = 1 / sqrt(S_kk) (0 where S_kk = 0)
             const float sq_r = sqrtf(S.sr);
             cpx<float> srow[NP];
 #pragma unroll
-            for (int k = 0; k < NP; ++k)
-                srow[k] = (live && k < n && S.rs[k] > 0.f) ? (sq_r / S.rs[k]) * S.crow[k] : mk<float>(0.f, 0.f);
+            for (int k = 0; k < NP; ++k) {
+                const float rk = sh.rsg[k];
+                srow[k] = (live && k < n && rk > 0.f) ? (sq_r / rk) * myrow[k] : mk<float>(0.f, 0.f);
+            }
             publish<NP, cpx<float>>(srow, smat, r, gmask);
         }
         float sd_mine = 0.f;  // this lane's date
         for (int i = 0; i < n; ++i) {
             if (i == ref) continue;  // uniform across the group
             cpx<float> h[NP];
-            adj_h_row<NP>(S, (r == i) ? 1.f : 0.f, r, n, ref, q.beta, cbuf, cmat, gmask, h);
+            adj_h_row<NP>(S, sh, (r == i) ? 1.f : 0.f, r, n, ref, q.beta, cbuf, cmat, gmask, h);
             // row r of M = H S, then <row r of H, row r of M>
             float tr = 0.f;
 #pragma unroll
@@ -759,10 +786,10 @@ template <int NP>
 static cudaError_t run_adj_uncert(const float2 *C, const float *Sd, int n, long long npx, int ref,
                                   const EmiParams &prm, float sigma2, float *out, cudaStream_t s) {
     constexpr int G = 32 / NP;
-    long long blocks = ((npx + G - 1) / G + kAdjWarps - 1) / kAdjWarps;
-    const long long cap = (long long)device_sm_count() * 16;
+    long long blocks = ((npx + G - 1) / G + kUncWarps - 1) / kUncWarps;
+    const long long cap = (long long)device_sm_count() * 32;
     blocks = std::max<long long>(1, std::min(blocks, cap));
-    k_adj_uncert<NP><<<(unsigned)blocks, kAdjWarps * 32, 0, s>>>(C, Sd, n, npx, ref, prm, sigma2, out);
+    k_adj_uncert<NP><<<(unsigned)blocks, kUncWarps * 32, 0, s>>>(C, Sd, n, npx, ref, prm, sigma2, out);
     return cudaGetLastError();
 }
 
