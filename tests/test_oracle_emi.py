@@ -188,6 +188,48 @@ def test_emi_matches_library_eigensolver_on_random_coherence():
         np.testing.assert_allclose(out["condG"][p], ge[-1] / ge[0], rtol=1e-8)
 
 
+@pytest.mark.parametrize("beta", [0.1, 0.5, 0.9])
+def test_regularised_emi_matches_library_eigensolver(beta):
+    # Sec. III-B's regularisation G = (1 - beta)|C| + beta I: the smallest
+    # eigenvector of G^-1 o C written out with numpy's inverse and eigh.
+    N, H, W = 7, 12, 16
+    window = (5, 11, 1, 1)
+    z = rand_stack(N, H, W, np.random.default_rng(3))
+    C = oracle.covariance(z, window, all_ones_mask(H, W, window)).reshape(-1, N * (N + 1) // 2)
+    out = oracle.phase_link(C, N, ref=2, beta=beta)
+    for p in range(C.shape[0]):
+        M = full_from_packed(C[p], N)
+        G = (1 - beta) * np.abs(M) + beta * np.eye(N)
+        w, V = np.linalg.eigh(np.linalg.inv(G) * M)
+        v = V[:, 0]
+        assert out["status"][p] == 0
+        np.testing.assert_allclose(out["lam"][p], w[0], rtol=1e-10)
+        np.testing.assert_allclose(wrapped(out["phase"][:, p] - np.angle(v * np.conj(v[2]))), 0, atol=1e-9)
+
+
+def test_regularisation_limit_beta_to_one():
+    # G^-1 = (1/beta)(I - ((1 - beta)/beta)|C|_off) + O((1 - beta)^2), so as
+    # beta -> 1 the smallest eigenvector of G^-1 o C tends to the largest one of
+    # |C| o C with its diagonal removed, the phase error shrinking like 1 - beta.
+    N, H, W = 7, 12, 16
+    window = (5, 11, 1, 1)
+    z = rand_stack(N, H, W, np.random.default_rng(3))
+    C = oracle.covariance(z, window, all_ones_mask(H, W, window)).reshape(-1, N * (N + 1) // 2)
+    errs = {}
+    for beta in (0.999, 0.9999):
+        out = oracle.phase_link(C, N, ref=2, beta=beta)
+        e = []
+        for p in range(C.shape[0]):
+            M = full_from_packed(C[p], N)
+            K = np.abs(M) * M
+            np.fill_diagonal(K, 0)
+            v = np.linalg.eigh(K)[1][:, -1]
+            e.append(np.abs(wrapped(out["phase"][:, p] - np.angle(v * np.conj(v[2])))).max())
+        errs[beta] = max(e)
+    assert errs[0.9999] < 1e-3
+    assert 5 < errs[0.999] / errs[0.9999] < 20
+
+
 def test_emi_rank_one_falls_back_to_evd():
     # One look: C = z z^H / |z_i||z_k|, |C| is the all-ones matrix (singular):
     # the inversion fails and the EVD fallback returns the phases of z.
