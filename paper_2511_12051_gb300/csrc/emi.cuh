@@ -304,11 +304,19 @@ __device__ __forceinline__ cpx<T> apply_A(const T (&g)[NP], const Loader &load, 
 // and returns the smallest pivot.  On return d = x^H a x of the last step
 // (1/(lambda - mu) for B^{-1}) and q the last convergence factor measured
 // above the noise floor.  Returns true on convergence.
+//
+// g_norm (>= ||G||_inf, 0 = none): when B for the starting shift is not
+// positive definite, the shift lies above lambda_min and the iteration would
+// converge to the eigenvalue nearest mu rather than the smallest one, so the
+// start is rebuilt once at 0.999 / g_norm, below lambda_min (lambda_min(G^-1 o C)
+// >= lambda_min(G^-1) min_i C_ii = 1 / lambda_max(G) >= 1 / ||G||_inf by Schur's
+// bound for a Hadamard product of positive semidefinite matrices), and the
+// reshifts move up from there.
 template <int NP, class T, class Reform>
 __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cpx<T> &d, T &mu, T &q,
                                                   const Reform &reform, bool allow_reshift, cpx<T> *cbuf, int r,
                                                   bool live, unsigned gmask, T tol, int max_iter,
-                                                  bool build_first) {
+                                                  bool build_first, T g_norm = T(0)) {
     const T tol2 = tol * tol;
     d = mk<T>(T(1), T(0));
     q = T(0);
@@ -319,7 +327,7 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
     // the old shift.  One call site keeps the inlined elimination code single.
     T mu_try = mu;
     int pending = build_first ? 2 : 0;  // 0 none, 1 try mu_try, 2 (re)build for mu
-    for (int it = 0; it < max_iter + 2 * 3; ++it) {
+    for (int it = 0; it < max_iter + 2 * 3 + 1; ++it) {
         if (pending) {
             const T pmin = reform(pending == 1 ? mu_try : mu);
             if (pending == 1 && pmin > T(0)) {
@@ -329,6 +337,10 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
             } else if (pending == 1) {
                 reshifts = 3;
                 pending = 2;
+                continue;
+            } else if (it == 0 && allow_reshift && !(pmin > T(0)) && g_norm > T(0)) {
+                // the starting shift is above lambda_min: rebuild below it
+                mu = fmin(mu, T(0.999) / g_norm);
                 continue;
             } else {
                 pending = 0;
@@ -455,7 +467,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     T q;
     auto reform = [&](T m) { return form_shift_inverse<NP, T>(a, g, load, m, cbuf, r, n, gmask); };
     const bool conv = inverse_iteration<NP, T>(a, x, d, mu, q, reform, !inv_failed, cbuf, r, live, gmask, tol,
-                                               prm.max_iter, !inv_failed);
+                                               prm.max_iter, !inv_failed, norm_g);
     if (!inv_failed && conv) {
         // Residual correction against A itself: x <- x - B^{-1} (A x - rho x).
         // Its fixed point is an exact eigenvector of A, whatever the rounding
@@ -553,6 +565,10 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
         if (prm.beta != 0.f) m = (1.0 - (double)prm.beta) * m + ((k == r) ? (double)prm.beta : 0.0);
         g[k] = m;
     }
+    double grow = 0.0;  // row r of |G| summed: ||G||_inf is the group maximum
+#pragma unroll
+    for (int k = 0; k < NP; ++k) grow += fabs(g[k]);
+    const float g_norm = (float)group_max<NP, double>(live ? grow : 0.0, gmask);
     const double minpiv =
         gj_invert<NP, double, double, true>(g, reinterpret_cast<double *>(dbuf), r, n, gmask, kPivotFail);
     double gs = 0.0;
@@ -608,7 +624,8 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
         }
         cpx<float> d;
         float q;
-        inverse_iteration<NP, float>(B, x, d, mu, q, formB, true, fbuf, r, live, gmask, 1e-6f, prm.max_iter, true);
+        inverse_iteration<NP, float>(B, x, d, mu, q, formB, true, fbuf, r, live, gmask, 1e-6f, prm.max_iter, true,
+                                     g_norm);
         // Tighten the preconditioner for the double-precision phase: shift to
         // just under lambda_min (by a tenth of the gap measured through q, at
         // most half the current distance), kept only if B stays positive
