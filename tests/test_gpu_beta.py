@@ -2,7 +2,8 @@
 beta > 0, against the FP64 oracle:
 
 - phase linking on coherences of the 128x128 and burst-shaped workloads:
-  phase within 1e-4 rad, gamma_t within 1e-5, no-data pixels alike;
+  phase within 1e-4 rad, gamma_t within 1e-5, no-data pixels alike; also
+  without regularisation for a caller's shift below or above lambda_min;
 - the adjoint: central finite differences of the oracle (h = 1e-6) on sampled
   samples (its (1 - beta) term of the G^-1 derivative is otherwise not
   exercised);
@@ -58,6 +59,25 @@ def test_regularised_phase_link_parity(plk, ctx, cfg, N, win, beta, ref):
     print(f"beta={beta}, N={N}: phase {rep}, EVD fallback {np.sum(o['status'] == 2)} of {live.sum()}")
     assert rep["max"] <= PHASE_TOL, rep
     assert np.nanmax(np.abs(tc[live] - o["tcoh"][live])) <= TCOH_TOL
+
+
+@pytest.mark.parametrize("mu", [0.5, 1.2, 3.0])
+def test_shift_above_or_below_lambda_min(plk, ctx, mu):
+    # A caller's shift far below lambda_min converges slowly but to the same
+    # eigenvector; one above it (lambda_min is near 1 without regularisation)
+    # must not converge to the eigenvalue nearest the shift.
+    N, win, ref = 10, (5, 11, 1, 1), 0
+    z, m = case(0, N, 40, 70, win, seed=9)
+    C = oracle.covariance(z, win, m).astype(np.complex64)
+    o = oracle.phase_link(C.astype(np.complex128), N, ref)
+    g = ctx.phase_link(torch.from_numpy(C).cuda(), N, ref, plk.default_params(mu=mu))
+    ph, st = to_np(g["phase"]), to_np(g["status"])
+    live = o["status"] != 3
+    clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0))) & (st != 4)
+    assert clear.sum() >= 0.98 * live.sum()
+    rep = phase_report(ph, o["phase"], clear)
+    print(f"mu={mu}: phase {rep}, not converged {np.sum(st == 4)}")
+    assert rep["max"] <= PHASE_TOL, rep
 
 
 def good_weights(o, seed):
