@@ -114,6 +114,28 @@ def test_phase_link_parity(ctx, cfg, N, ref):
     assert (clear.sum() >= 0.98 * live.sum())
 
 
+@pytest.mark.parametrize("cfg,N,ref", [(1, 15, 0), (2, 15, 3)])
+def test_phase_link_without_fp64_resolve(plk, ctx, cfg, N, ref):
+    # fp64_resolve = 0 keeps every pixel in single precision: no pixel reports
+    # the double-precision status, and every pixel the default mode also
+    # solves in single precision gets the same answer (same kernel, same path).
+    win = (5, 11, 3, 6) if cfg == 1 else (5, 11, 1, 1)
+    C32 = oracle_C(cfg, N, 60, 90, win, seed=40 + cfg)
+    Cg = torch.from_numpy(C32).cuda()
+    d = ctx.phase_link(Cg, N, ref)
+    s = ctx.phase_link(Cg, N, ref, plk.default_params(fp64_resolve=0))
+    st_d, st_s = to_np(d["status"]), to_np(s["status"])
+    assert not np.any(st_s == 1)
+    same = st_d == 0
+    assert np.array_equal(st_s[same], st_d[same])
+    assert np.array_equal(to_np(s["phase"])[:, same], to_np(d["phase"])[:, same])
+    o = oracle.phase_link(C32.astype(np.complex128), N, ref)
+    clear = same & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+    assert phase_report(to_np(s["phase"]), o["phase"], clear)["max"] <= PHASE_TOL
+    print(f"cfg{cfg}: {np.sum(st_d == 1)} pixels re-solved in double precision by default, "
+          f"statuses without: {np.bincount(st_s.ravel(), minlength=5).tolist()}")
+
+
 def test_phase_link_closed_forms(ctx):
     # N=2: linked phase = interferogram phase, gamma_t = 1, lambda_min = 1.
     rng = np.random.default_rng(5)
