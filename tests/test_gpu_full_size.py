@@ -121,3 +121,73 @@ def test_sampled_compressed_slc_at_full_size(burst):
         kc = to_np(kg[oy * sy:(oy + 1) * sy, ox * sx:(ox + 1) * sx])
         scale = np.abs(cell).sum(0)
         assert np.max(np.abs(kc - ko) / (scale + 1e-6)) < 1e-4, (oy, ox)
+
+
+# ------------------------------------------------ sequential chain, full size
+
+CHAIN_WINDOW = (5, 11, 1, 1)
+CHAIN_K_MAX, CHAIN_M = 3, 15
+
+
+@pytest.fixture(scope="module")
+def chain(plk):
+    """Four mini-stack steps of the 60-date 2048 x 4096 chain (a +2 rad step
+    from date 31 on a 200 x 200 patch), outputs kept at sampled pixels."""
+    ctx = plk.Context("cuda:0")
+    spec = synth.config_spec(3)
+    z = synth.generate(spec, device="cuda")
+    H, W = spec.H, spec.W
+    rng = np.random.default_rng(60)
+    pix = [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0)]
+    pix += [(int(rng.integers(H)), int(rng.integers(W))) for _ in range(40)]
+    pix += [(int(rng.integers(924, 1124)), int(rng.integers(1948, 2148))) for _ in range(16)]   # the step patch
+    ys = torch.tensor([p[0] for p in pix], device="cuda")
+    xs = torch.tensor([p[1] for p in pix], device="cuda")
+    st = plk.State(ctx, H, W, CHAIN_WINDOW, K_max=CHAIN_K_MAX, M_max=CHAIN_M)
+    steps = []
+    for sl in synth.ministack_slices(spec.N, CHAIN_M):
+        g = st.step(z[sl].contiguous())
+        steps.append({"phase": to_np(g["phase"][:, ys, xs]), "tcoh": to_np(g["tcoh"][ys, xs]),
+                      "status": to_np(g["status"][ys, xs]), "count": count_np(g["count"][ys, xs])})
+    kap = [to_np(st.kappa(i)[ys, xs]) for i in range(st.info()["K_used"])]
+    yield {"z": z, "H": H, "W": W, "N": spec.N, "pix": pix, "steps": steps, "kappa": kap}
+    st.close()
+    del z
+    torch.cuda.empty_cache()
+
+
+def test_chain_sampled_at_full_size(chain):
+    # An output of step k reaches back through the compressed SLCs of the
+    # earlier steps, each a window further: after four steps, 4 * 2 rows and
+    # 4 * 5 columns.  The oracle runs the whole chain on a crop with that
+    # margin (and two more) around each sampled pixel.
+    wy, wx, _, _ = CHAIN_WINDOW
+    my, mx = 4 * (wy // 2) + 2, 4 * (wx // 2) + 2
+    H, W, Nd = chain["H"], chain["W"], chain["N"]
+    diffs, tcd = [], []
+    for j, (py, px) in enumerate(chain["pix"]):
+        y0, y1 = max(0, py - my), min(H, py + my + 1)
+        x0, x1 = max(0, px - mx), min(W, px + mx + 1)
+        crop = chain["z"][:, y0:y1, x0:x1].cpu().numpy()
+        orc = oracle.OracleChain(y1 - y0, x1 - x0, CHAIN_WINDOW, K_max=CHAIN_K_MAX, alpha=1e-3)
+        ly, lx = py - y0, px - x0
+        for k, sl in enumerate(synth.ministack_slices(Nd, CHAIN_M)):
+            o = orc.step(crop[sl])
+            g = chain["steps"][k]
+            assert g["count"][j] == o["count"][ly, lx], (j, k)
+            if o["status"][ly, lx] == 3:
+                assert g["status"][j] == 3
+                continue
+            K = o["K_used"]
+            diffs.append(wrapped_diff(g["phase"][:, j], o["phase"][K:, ly, lx]).max())
+            tcd.append(abs(g["tcoh"][j] - o["tcoh"][ly, lx]))
+        for i, ko in enumerate(orc.ring):
+            scale = np.abs(crop[:, ly, lx]).sum()
+            assert abs(chain["kappa"][i][j] - ko[ly, lx]) <= 1e-3 * scale, (j, i)
+    diffs, tcd = np.array(diffs), np.array(tcd)
+    print(f"chain at full size: {len(chain['pix'])} pixels x 4 steps, phase max {diffs.max():.2e} "
+          f"p99 {np.percentile(diffs, 99):.2e} median {np.median(diffs):.2e} rad, gamma_t max {tcd.max():.2e}")
+    # each side carries its own compressed SLCs, so the bar is the chain's statistical one
+    assert np.percentile(diffs, 99) <= PHASE_TOL
+    assert np.median(diffs) <= 0.1 * PHASE_TOL
+    assert np.percentile(tcd, 99) <= TCOH_TOL
