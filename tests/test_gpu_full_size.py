@@ -191,3 +191,147 @@ def test_chain_sampled_at_full_size(chain):
     assert np.percentile(diffs, 99) <= PHASE_TOL
     assert np.median(diffs) <= 0.1 * PHASE_TOL
     assert np.percentile(tcd, 99) <= TCOH_TOL
+
+
+# ------------------------------------------------- uneven batch, full size
+
+def test_batch_sampled_at_full_size(plk):
+    # The batch workload as timed: 64 stacks of 1024 x 2048, N from 5..30,
+    # gamma0 from 0.3..0.9, 1% near-singular patches, one recorded graph.
+    from paper_2511_12051_gb300 import dist as pdist
+    ctx = plk.Context("cuda:0")
+    rng = np.random.default_rng(pdist.unit_seed(2, 0))
+    Ns = rng.integers(5, 31, 64)
+    g0 = rng.uniform(0.3, 0.9, 64)
+    zs = [synth.generate(synth.config_spec(2, N=int(Ns[i]), rho0=float(g0[i]), seed=int(rng.integers(1 << 30)),
+                                           H=1024, W=2048), device="cuda") for i in range(64)]
+    b = plk.Batch(ctx, zs, WINDOW)
+    b.run()          # tunes and records
+    out = b.run()    # the recorded graph
+    torch.cuda.synchronize()
+    srng = np.random.default_rng(5)
+    diffs, n_fp64, n_evd = [], 0, 0
+    for i, (z, o_g) in enumerate(zip(zs, out)):
+        st = to_np(o_g["status"])
+        Ho, Wo = st.shape
+        pix = [(int(srng.integers(Ho)), int(srng.integers(Wo))) for _ in range(3)]
+        for code in (1, 2):
+            ys, xs = np.nonzero(st == code)
+            if ys.size:
+                j = int(srng.integers(ys.size))
+                pix.append((int(ys[j]), int(xs[j])))
+        ph, tc = to_np(o_g["phase"]), to_np(o_g["tcoh"])
+        bdict = {"z": z, "H": 1024, "W": 2048}
+        for oy, ox in pix:
+            o = oracle_pixel_n(bdict, oy, ox, int(Ns[i]))
+            assert (o["status"] == 3) == (st[oy, ox] == 3), (i, oy, ox)   # the batch reports no SHP counts
+            if o["status"] == 3 or st[oy, ox] == 4:
+                continue
+            assert (st[oy, ox] == 2) == (o["status"] == 2), (i, oy, ox)
+            n_fp64 += int(st[oy, ox] == 1)
+            n_evd += int(st[oy, ox] == 2)
+            if o["gap"] > 1e-6 * abs(o["lam"] if np.isfinite(o["lam"]) else 1.0):
+                d = wrapped_diff(ph[:, oy, ox], o["phase"]).max()
+                diffs.append(d)
+                assert d <= PHASE_TOL, (i, oy, ox, d)
+            assert abs(tc[oy, ox] - o["tcoh"]) <= TCOH_TOL, (i, oy, ox)
+    print(f"batch at full size: {len(diffs)} pixels compared over 64 stacks ({n_fp64} double-precision, "
+          f"{n_evd} EVD), max phase error {max(diffs):.2e} rad")
+    assert len(diffs) >= 64 * 3
+    b.close()
+    del zs
+    torch.cuda.empty_cache()
+
+
+def oracle_pixel_n(b, oy, ox, n):
+    """oracle_pixel for a stack of n dates (reference date 0)."""
+    wy, wx, sy, sx = WINDOW
+    hy, hx = wy // 2, wx // 2
+    cy, cx = oy * sy + sy // 2, ox * sx + sx // 2
+    y0, y1 = max(0, cy - hy), min(b["H"], cy + hy + 1)
+    x0, x1 = max(0, cx - hx), min(b["W"], cx + hx + 1)
+    crop = b["z"][:, y0:y1, x0:x1].cpu().numpy()
+    win1 = (wy, wx, 1, 1)
+    P, _ = oracle.amp_stats(crop)
+    m, cnt = oracle.shp_select(P, win1, np.float32(oracle.glrt_threshold(1e-3, n)))
+    C = oracle.covariance(crop, win1, m)[cy - y0, cx - x0]
+    o = oracle.phase_link(C[None], n, 0)
+    return {"count": int(cnt[cy - y0, cx - x0]), "phase": o["phase"][:, 0], "tcoh": o["tcoh"][0],
+            "status": int(o["status"][0]), "gap": o["gap"][0], "lam": o["lam"][0]}
+
+
+# ------------------------------------------------------ adjoint, full size
+
+def test_adjoint_sampled_at_full_size(plk):
+    # The adjoint workload as timed: N = 20 x 1024 x 1024, 11x5 window, stride
+    # 1, masks frozen, L = sum(w * phase), w ~ U(-1, 1).  The gradient at a
+    # sample q sums over the output pixels whose windows hold q (rows q +- 2,
+    # columns q +- 5), each depending on its own window: a crop of q +- 4 rows
+    # and +- 10 columns (plus 1) holds all of it.  Oracle: central differences
+    # (h = 1e-6) of that partial loss, with the crop's own oracle SHP masks
+    # (checked equal to the library's); the weights of pixels the oracle finds
+    # near the wrap or off the EMI path are set to 0 on both sides.
+    ctx = plk.Context("cuda:0")
+    win = (5, 11, 1, 1)
+    spec = synth.config_spec(4)
+    z = synth.generate(spec, device="cuda")
+    Nd, H, W = z.shape
+    P, _ = ctx.amp_stats(z)
+    mask, _ = ctx.shp_select(P, Nd, win, 1e-3)
+    g = torch.Generator(device="cuda").manual_seed(4)
+    wn = to_np(torch.rand((Nd, H, W), device="cuda", generator=g) * 2 - 1)
+    srng = np.random.default_rng(20)
+    qs = [(int(srng.integers(H)), int(srng.integers(W))) for _ in range(12)] + [(0, 0), (H - 1, W - 1)]
+    nb = win[0] * win[1]
+    thr = np.float32(oracle.glrt_threshold(1e-3, Nd))
+    mk = to_np(mask).view(np.uint64)
+    cases = []
+    for (qy, qx) in qs:
+        y0, y1 = max(0, qy - 5), min(H, qy + 6)
+        x0, x1 = max(0, qx - 11), min(W, qx + 12)
+        crop = z[:, y0:y1, x0:x1].cpu().numpy().astype(np.complex128)
+        Pc, _ = oracle.amp_stats(crop.astype(np.complex64))
+        mc, _ = oracle.shp_select(Pc, win, thr)   # stride 1: crop pixel (i, j) is output (i, j)
+        py0, py1 = max(0, qy - 2), min(H, qy + 3)   # output pixels whose windows hold q
+        px0, px1 = max(0, qx - 5), min(W, qx + 6)
+        for py in range(py0, py1):
+            for px in range(px0, px1):
+                assert np.array_equal(mk[py, px], mc[py - y0, px - x0]), (py, px)
+                s, _ = oracle.window_samples(crop, win, py - y0, px - x0)   # all in-image samples are in the crop
+                o = oracle.phase_link(oracle.weighted_coherence(s, oracle.mask_weights(mc[py - y0, px - x0], nb))[None],
+                                      Nd, 0)
+                if o["status"][0] != 0 or np.any(np.abs(o["phase"][:, 0]) > np.pi - 0.05):
+                    wn[:, py, px] = 0.0          # ill-posed: no weight on either side
+        cases.append((qy, qx, y0, x0, py0, py1, px0, px1, crop, mc))
+    grad = to_np(ctx.phase_link_backward(z, win, mask, 0, torch.from_numpy(wn).cuda(),
+                                         plk.default_params(fp64_resolve=0)))
+    errs, refs = [], []
+    h = 1e-6
+    for (qy, qx, y0, x0, py0, py1, px0, px1, crop, mc) in cases:
+        def loss(zc):
+            tot = 0.0
+            for py in range(py0, py1):
+                for px in range(px0, px1):
+                    if not np.any(wn[:, py, px]):
+                        continue
+                    s, _ = oracle.window_samples(zc, win, py - y0, px - x0)
+                    Cw = oracle.weighted_coherence(s, oracle.mask_weights(mc[py - y0, px - x0], nb))
+                    tot += float(np.dot(wn[:, py, px], oracle.phase_link(Cw[None], Nd, 0)["phase"][:, 0]))
+            return tot
+
+        ly, lx = qy - y0, qx - x0
+        for i in srng.choice(Nd, size=2, replace=False):
+            for comp in (1.0, 1j):
+                zp, zm = crop.copy(), crop.copy()
+                zp[i, ly, lx] += h * comp
+                zm[i, ly, lx] -= h * comp
+                fd = (loss(zp) - loss(zm)) / (2 * h)
+                ad = grad[i, qy, qx].real if comp == 1.0 else grad[i, qy, qx].imag
+                errs.append(abs(ad - fd))
+                refs.append(abs(fd))
+    errs, refs = np.array(errs), np.array(refs)
+    print(f"adjoint at full size: {errs.size} gradient components, max abs err {errs.max():.2e}, "
+          f"max |grad| {refs.max():.2e}")
+    assert np.all(errs <= 1e-3 * max(refs.max(), 1e-6) + 5e-3 * refs)
+    del z
+    torch.cuda.empty_cache()
