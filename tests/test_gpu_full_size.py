@@ -1,18 +1,21 @@
-"""Parity at the full burst size, in the launch configuration the bench times.
+"""Parity at the full sizes of the five workloads, in the launch
+configurations the bench times, on outputs the FP64 oracle recomputes one by
+one from crops of the same inputs (every local input of an output lies in a
+crop around it; each crop oracle is checked exact against the whole-image
+oracle on small stacks):
 
-One mini-stack step on the burst-shaped workload (N = 15 complex64 SLCs of
-4096 x 16384 pixels, 11x5 window, output strides 6x3, default parameters, a
-state with room for 6 compressed SLCs and 15 new ones), then sampled outputs
-recomputed one by one by the FP64 oracle from crops of the same stack:
+- burst (N = 15, 4096 x 16384, 11x5, strides 6x3): sampled output pixels
+  (random, corners, double-precision and EVD pixels) and compressed-SLC cells;
+- sequential chain (60 dates of 2048 x 4096 in four mini-stacks): sampled
+  pixels through every step, the crop holding the dependency cone;
+- uneven batch (64 stacks, N = 5..30, recorded graph): sampled pixels;
+- adjoint (N = 20, 1024 x 1024): sampled gradient components against central
+  differences of the oracle's partial loss;
+- the 128 x 128 stack: every pixel.
 
-- output pixels (random, the four corners, and pixels the library sent to the
-  EVD fallback or the double-precision re-solve): SHP count bit-exact, no-data
-  and EVD decisions alike, phase within 1e-4 rad, gamma_t within 1e-5;
-- output cells: the compressed SLC at their 3 x 6 full-resolution pixels.
-
-Every local quantity the oracle needs lies inside a crop around the pixel:
-the amplitude sums are per pixel, and the SHP test, the coherence and the
-compression only reach the pixel's window or cell.
+SHP counts bit-exact, EVD and no-data decisions alike, phase within 1e-4 rad,
+gamma_t within 1e-5 (statistical bars for the chain, whose sides carry their
+own compressed SLCs).
 """
 import numpy as np
 import pytest
@@ -335,3 +338,31 @@ def test_adjoint_sampled_at_full_size(plk):
     assert np.all(errs <= 1e-3 * max(refs.max(), 1e-6) + 5e-3 * refs)
     del z
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------ 128 x 128 stack, every pixel
+
+def test_small_stack_every_pixel(plk):
+    # N = 10 x 128 x 128, 11x5 window, stride 1, GLRT at alpha = 1e-3: the
+    # whole image through one step against the whole-image oracle.
+    ctx = plk.Context("cuda:0")
+    win = (5, 11, 1, 1)
+    z = synth.generate(synth.config_spec(0))
+    Nd, H, W = z.shape
+    assert (Nd, H, W) == (10, 128, 128)
+    st = plk.State(ctx, H, W, win, K_max=6, M_max=Nd)
+    g = st.step(z.cuda())
+    orc = oracle.OracleChain(H, W, win, K_max=6, alpha=1e-3, kappa_dtype=np.complex64)
+    o = orc.step(z.numpy())
+    assert np.array_equal(count_np(g["count"]), o["count"])
+    live = o["status"] != 3
+    assert np.array_equal(to_np(g["status"]) == 3, ~live)
+    clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+    assert clear.sum() >= 0.99 * live.sum()
+    d = wrapped_diff(to_np(g["phase"]), o["phase"][o["K_used"]:])[:, clear]
+    assert d.max() <= PHASE_TOL, d.max()
+    assert np.abs(to_np(g["tcoh"]) - o["tcoh"])[live].max() <= TCOH_TOL
+    kg = to_np(st.kappa(st.info()["K_used"] - 1))
+    assert np.max(np.abs(kg - orc.ring[-1]) / (np.abs(z.numpy()).sum(0) + 1e-6)) < 1e-4
+    print(f"128x128: {clear.sum()} of {live.sum()} pixels compared, max phase error {d.max():.2e} rad")
+    st.close()
