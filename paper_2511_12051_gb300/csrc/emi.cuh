@@ -142,6 +142,25 @@ __device__ __forceinline__ cpx<T> real_s(cpx<T>, T v) { return mk<T>(v, T(0)); }
 // pivot (in step order, over the first n steps, before replacement) that is
 // <= thr -- the one a Cholesky factorisation would stop at -- or, if there is
 // none, the smallest pivot.
+// a[c] <- a[(c + s) mod NP] for a group-uniform 0 <= s < NP: one conditional
+// rotation per bit of s (NP moves each) instead of s single-place shifts.
+template <int NP, class S>
+__device__ __forceinline__ void rotate_left(S (&a)[NP], int s) {
+#pragma unroll
+    for (int b = NP / 2; b >= 1; b >>= 1) {
+        if (s & b) {
+            // b cycles of NP / b entries, one temporary each
+#pragma unroll
+            for (int c = 0; c < b; ++c) {
+                const S t = a[c];
+#pragma unroll
+                for (int i = 0; i + 1 < NP / b; ++i) a[c + i * b] = a[c + (i + 1) * b];
+                a[c + NP - b] = t;
+            }
+        }
+    }
+}
+
 template <int NP, class T, class S, bool PD>
 __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigned gmask, T thr) {
     constexpr int E = 16 / sizeof(S);
@@ -150,16 +169,7 @@ __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigne
     T first_low = Lim<T>::big;
     bool have_low = false;
 #pragma unroll 1
-    for (int k = 0; k < NP; ++k) {
-        const S zero = real_s(a[0], T(0)), one = real_s(a[0], T(1));
-        if (k >= n) {
-            // Padded pivot (identity row and column): f' = 0 on every lane,
-            // the step only rotates the rows.
-#pragma unroll
-            for (int j = 1; j < NP; ++j) a[j - 1] = a[j];
-            a[NP - 1] = (r == k) ? one : zero;
-            continue;
-        }
+    for (int k = 0; k < n; ++k) {
         const bool pivot_lane = (r == k);
         if (pivot_lane) {
             uint4 *dst = reinterpret_cast<uint4 *>(buf);
@@ -208,6 +218,10 @@ __device__ __forceinline__ T gj_invert(S (&a)[NP], S *buf, int r, int n, unsigne
         a[NP - 1] = pivot_lane ? real_s(a[0], inv) : neg_s(fp);
         __syncwarp(gmask);
     }
+    // Padded pivots k >= n (identity row and column): f' = 0 on every lane and
+    // the entry rotated in is the one rotated out, so each such step is a
+    // rotation by one place; all of them together, a rotation by NP - n.
+    rotate_left<NP, S>(a, NP - n);
     return have_low ? first_low : minpiv;
 }
 
