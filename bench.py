@@ -364,6 +364,112 @@ def run_adjoint(args, rank: int, world: int, local: int):
     return 0
 
 
+def run_chain(args, rank: int, world: int, local: int):
+    """Sequential chain: 60 dates of 2048x4096 (the +2 rad patch from date 31)
+    through four mini-stacks of 15 new SLCs, stride 1, keeping 3 compressed
+    SLCs (N = 15, 16, 17, 18 per step).  Each timed pass runs the whole chain
+    from a reset state; reported per step and for the chain."""
+    import torch
+    from paper_2511_12051_gb300 import build, synth, plk
+    from paper_2511_12051_gb300 import dist as pdist
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spec = synth.config_spec(3, seed=pdist.unit_seed(3, rank))
+    z = synth.generate(spec, device=dev)
+    win, K_max, M = (5, 11, 1, 1), 3, 15
+    slices = synth.ministack_slices(spec.N, M)
+    parts = [z[sl].contiguous() for sl in slices]
+    stream = torch.cuda.Stream(dev)
+    ctx = plk.Context(dev, stream)
+    st = plk.State(ctx, spec.H, spec.W, win, K_max=K_max, M_max=M)
+    with torch.cuda.stream(stream):
+        outs = []
+        for zz in parts:
+            outs.append(st.step(zz))
+    torch.cuda.synchronize(dev)
+    npx = st.Ho * st.Wo
+
+    def chain():
+        st.reset()
+        for zz, o in zip(parts, outs):
+            st.step(zz, out=o)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            chain()
+    torch.cuda.synchronize(dev)
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pdist.barrier()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            chain()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_chain = pdist.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    stages = {kk: v[0] / args.steps for kk, v in ctx.profile_collect().items()}
+    ctx.profile(False)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": len(slices) * npx * world / (ms_chain / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_chain,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sequential chain: 60 dates of 2048x4096 (+2 rad patch from date 31), 4 mini-stacks "
+                                   "of 15, K_max 3 (N = 15..18 per step), 11x5 window, stride 1",
+                       "output_px_per_step": npx, "steps_per_chain": len(slices)},
+            "ms_per_chain": ms_chain, "ms_per_ministack_step": ms_chain / len(slices),
+            "stages_ms_per_chain": stages}), flush=True)
+    st.close()
+    return 0
+
+
+def run_small(args, rank: int, world: int, local: int):
+    """The 128x128 stack (N = 10, 11x5 window, stride 1): launch- and
+    latency-bound; one step reported in microseconds and pixels/s."""
+    import torch
+    from paper_2511_12051_gb300 import build, synth, plk
+    from paper_2511_12051_gb300 import dist as pdist
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    z = synth.generate(synth.config_spec(0, seed=pdist.unit_seed(0, rank)), device=dev)
+    stream = torch.cuda.Stream(dev)
+    ctx = plk.Context(dev, stream)
+    st = plk.State(ctx, 128, 128, (5, 11, 1, 1), K_max=6, M_max=10)
+    with torch.cuda.stream(stream):
+        out = st.step(z)
+    torch.cuda.synchronize(dev)
+
+    def one():
+        st.reset()
+        st.step(z, out=out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 100)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            one()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = pdist.max_over_ranks(e0.elapsed_time(e1) / reps, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": 128 * 128 * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": reps, "warmup": args.warmup, "ms_per_step": ms, "us_per_step": ms * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "N=10 x 128x128, 11x5 window, stride 1 (launch- and latency-bound)",
+                       "output_px_per_gpu": 128 * 128}}), flush=True)
+    st.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,9 +487,10 @@ def main():
                     help="skip timing the reduced-precision, PS, gamma_s and L1-inversion modes beside it")
     ap.add_argument("--ps-da-max", type=float, default=0.0,
                     help="PS threshold on the amplitude dispersion in the timed step (0: no PS regridding)")
-    ap.add_argument("--workload", default="burst", choices=["burst", "batch", "adjoint"],
+    ap.add_argument("--workload", default="burst", choices=["burst", "batch", "adjoint", "chain", "small"],
                     help="burst: the headline mini-stack step; batch: 64 uneven stacks in one recorded graph; "
-                         "adjoint: forward and backward of the phase linking on N=20 x 1024x1024")
+                         "adjoint: forward and backward of the phase linking on N=20 x 1024x1024; chain: 60 dates "
+                         "of 2048x4096 in four mini-stacks; small: N=10 x 128x128")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -397,6 +504,10 @@ def main():
         return run_batch(args, rank, world, local)
     if args.workload == "adjoint":
         return run_adjoint(args, rank, world, local)
+    if args.workload == "chain":
+        return run_chain(args, rank, world, local)
+    if args.workload == "small":
+        return run_small(args, rank, world, local)
 
     import torch
     import torch.distributed as dist
