@@ -45,22 +45,31 @@ template <> struct Lim<double> {
 constexpr double kPivotFail = 1e-4;
 constexpr double kPivotBand = 2e-5;
 
+// Lanes a group's reductions span: NP when it is a power of two; otherwise
+// (rows of 24 entries) the whole warp, one pixel a warp, the lanes past the
+// last row contributing the reduction's identity (their rows are all zero, and
+// every caller passes 0, or the identity, for rows past n).
+template <int NP>
+struct GroupLanes {
+    static constexpr int value = (NP & (NP - 1)) ? 32 : NP;
+};
+
 template <int NP, class T>
 __device__ __forceinline__ T group_sum(T v, unsigned gmask) {
 #pragma unroll
-    for (int off = NP / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(gmask, v, off);
+    for (int off = GroupLanes<NP>::value / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(gmask, v, off);
     return v;
 }
 template <int NP, class T>
 __device__ __forceinline__ T group_max(T v, unsigned gmask) {
 #pragma unroll
-    for (int off = NP / 2; off >= 1; off >>= 1) v = fmax(v, __shfl_xor_sync(gmask, v, off));
+    for (int off = GroupLanes<NP>::value / 2; off >= 1; off >>= 1) v = fmax(v, __shfl_xor_sync(gmask, v, off));
     return v;
 }
 template <int NP, class T>
 __device__ __forceinline__ T group_min(T v, unsigned gmask) {
 #pragma unroll
-    for (int off = NP / 2; off >= 1; off >>= 1) v = fmin(v, __shfl_xor_sync(gmask, v, off));
+    for (int off = GroupLanes<NP>::value / 2; off >= 1; off >>= 1) v = fmin(v, __shfl_xor_sync(gmask, v, off));
     return v;
 }
 
@@ -146,16 +155,29 @@ __device__ __forceinline__ cpx<T> real_s(cpx<T>, T v) { return mk<T>(v, T(0)); }
 // rotation per bit of s (NP moves each) instead of s single-place shifts.
 template <int NP, class S>
 __device__ __forceinline__ void rotate_left(S (&a)[NP], int s) {
+    if constexpr ((NP & (NP - 1)) == 0) {
 #pragma unroll
-    for (int b = NP / 2; b >= 1; b >>= 1) {
-        if (s & b) {
-            // b cycles of NP / b entries, one temporary each
+        for (int b = NP / 2; b >= 1; b >>= 1) {
+            if (s & b) {
+                // b cycles of NP / b entries, one temporary each
 #pragma unroll
-            for (int c = 0; c < b; ++c) {
-                const S t = a[c];
+                for (int c = 0; c < b; ++c) {
+                    const S t = a[c];
 #pragma unroll
-                for (int i = 0; i + 1 < NP / b; ++i) a[c + i * b] = a[c + (i + 1) * b];
-                a[c + NP - b] = t;
+                    for (int i = 0; i + 1 < NP / b; ++i) a[c + i * b] = a[c + (i + 1) * b];
+                    a[c + NP - b] = t;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int b = 16; b >= 1; b >>= 1) {
+            if (b < NP && (s & b)) {
+                S t[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) t[j] = a[(j + b) % NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) a[j] = t[j];
             }
         }
     }

@@ -59,21 +59,30 @@ __device__ __forceinline__ long long next_chunk(unsigned long long *counter, int
 
 // Single-precision pass: one NP-lane group per pixel.  Pixels the solve flags
 // get status kPending and no other output.
+// Rows of 24 entries (17 <= N <= 24) run one pixel a warp with lanes 24-31
+// idle: fewer registers than 32-entry rows (three CTAs an SM instead of two)
+// and a quarter fewer updates per elimination step.
 template <int NP>
-__global__ void __launch_bounds__(kEmiWarps * 32, NP == 32 ? 1 : PLK_EMI_MINB) k_emi32(const float2 *__restrict__ C, int n, long long npx,
+struct EmiMinBlocks {
+    static constexpr int value = NP == 32 ? 1 : (NP == 24 ? 3 : PLK_EMI_MINB);
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi32(const float2 *__restrict__ C, int n, long long npx,
                                                           int ref, const EmiParams prm,
                                                           float *__restrict__ phase, float *__restrict__ tcoh,
                                                           float *__restrict__ lam, uint8_t *__restrict__ status) {
-    constexpr int G = 32 / NP;
+    constexpr bool kPow2 = (NP & (NP - 1)) == 0;
+    constexpr int G = kPow2 ? 32 / NP : 1;
     // Complex entries per cached row: NP + 2 (16-byte aligned rows whose
     // 16-byte chunks fall in different banks for 8 consecutive lanes).
     constexpr int kRowPitch = NP + 2;
     __shared__ __align__(16) cpx<float> sbuf[kEmiWarps][32];
     __shared__ __align__(16) cpx<float> rowcache[kEmiWarps * 32 * kRowPitch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / NP, r = lane - grp * NP;
+    const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
     const long long step = (long long)gridDim.x * kEmiWarps * G;
     cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
@@ -298,7 +307,8 @@ template <int NP>
 static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const EmiParams &prm, float *phase,
                            float *tcoh, float *lam, uint8_t *status, cudaStream_t s, Prof *prof,
                            const StackSource *src) {
-    constexpr int G = 32 / NP;
+    constexpr int G = (NP & (NP - 1)) ? 1 : 32 / NP;
+    constexpr int NP64 = (NP & (NP - 1)) ? 32 : NP;  // the double-precision re-solve keeps power-of-two groups
     const long long cap = (long long)device_sm_count() * 16;
     long long blocks = ((npx + G - 1) / G + kEmiWarps - 1) / kEmiWarps;
     blocks = blocks > cap ? cap : (blocks < 1 ? 1 : blocks);
@@ -313,10 +323,10 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
     if (prof) prof->begin("phase_link_fp64", s);
     k_reset_counter<<<1, 1, 0, s>>>(prm.work);
     if (src)
-        k_emi64_stack<NP><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(*src->z, *src->g, src->mask, n, npx, ref, prm,
-                                                                        phase, tcoh, lam, status);
+        k_emi64_stack<NP64><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(*src->z, *src->g, src->mask, n, npx, ref,
+                                                                          prm, phase, tcoh, lam, status);
     else
-        k_emi64<NP><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status);
+        k_emi64<NP64><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status);
     e = cudaGetLastError();
     if (prof) prof->end(s);
     return e;
@@ -328,10 +338,11 @@ cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, co
     if (npx == 0) return cudaSuccess;
     // Lanes per pixel: the smallest group that holds a row, unless the
     // schedule asks for a wider one (fewer pixels per warp).
-    int np = n <= 8 ? 8 : (n <= 16 ? 16 : 32);
-    if (sch && sch->emi_np >= np && (sch->emi_np == 16 || sch->emi_np == 32)) np = sch->emi_np;
+    int np = n <= 8 ? 8 : (n <= 16 ? 16 : (n <= 24 ? 24 : 32));
+    if (sch && sch->emi_np >= np && (sch->emi_np == 16 || sch->emi_np == 24 || sch->emi_np == 32)) np = sch->emi_np;
     if (np == 8) return run_emi<8>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
     if (np == 16) return run_emi<16>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+    if (np == 24) return run_emi<24>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
     return run_emi<32>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
 }
 

@@ -64,7 +64,7 @@ cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *m
 // Launch schedule chosen by the batch autotuner (0 = the built-in heuristic).
 struct Schedule {
     int cov_TY = 0, cov_TX = 0;  // single-precision coherence tile (output pixels)
-    int emi_np = 0;              // lanes per pixel in the EMI kernels (8, 16 or 32, >= n)
+    int emi_np = 0;              // row length of the EMI kernels (8, 16, 24 or 32, >= n)
 };
 
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
