@@ -278,16 +278,17 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_pixel(const float2 *__re
                                                               int ref, const EmiParams prm,
                                                               const float *__restrict__ w,
                                                               float2 *__restrict__ Hout) {
-    constexpr int G = 32 / NP;
+    constexpr bool kPow2 = (NP & (NP - 1)) == 0;
+    constexpr int G = kPow2 ? 32 / NP : 1;
     constexpr int kRowPitch = NP + 2;
     constexpr int kGrpBuf = 2 * NP + 2;
     __shared__ __align__(16) cpx<float> sbuf[kAdjWarps][G * kGrpBuf];
     __shared__ __align__(16) cpx<float> rowcache[kAdjWarps * 32 * kRowPitch];
     __shared__ __align__(16) cpx<float> mats[kAdjWarps][32 * NP];  // one NP x NP matrix per group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / NP, r = lane - grp * NP;
+    const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;  // 24-entry rows: one pixel a warp
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
     const long long step = (long long)gridDim.x * kAdjWarps * G;
     cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
@@ -476,7 +477,8 @@ __global__ void __launch_bounds__(kUncWarps * 32) k_adj_uncert(const float2 *__r
                                                                const float *__restrict__ Sd, int n, long long npx,
                                                                int ref, const EmiParams prm, float sigma2,
                                                                float *__restrict__ sd_out) {
-    constexpr int G = 32 / NP;
+    constexpr bool kPow2 = (NP & (NP - 1)) == 0;
+    constexpr int G = kPow2 ? 32 / NP : 1;
     constexpr int kRowPitch = NP + 2;
     constexpr int kGrpBuf = 2 * NP + 2;
     __shared__ __align__(16) cpx<float> sbuf[kUncWarps][G * kGrpBuf];
@@ -487,9 +489,9 @@ __global__ void __launch_bounds__(kUncWarps * 32) k_adj_uncert(const float2 *__r
     __shared__ __align__(16) cpx<float> vs[kUncWarps][32];
     __shared__ __align__(16) float rss[kUncWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / NP, r = lane - grp * NP;
+    const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;  // 24-entry rows: one pixel a warp
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
     const long long step = (long long)gridDim.x * kUncWarps * G;
     cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
@@ -774,7 +776,7 @@ static int adj_grid(long long work) {
 template <int NP>
 static cudaError_t run_adj_pixel(const float2 *C, const float *Sd, int n, long long npx, int ref,
                                  const EmiParams &prm, const float *w, float2 *H, cudaStream_t s) {
-    constexpr int G = 32 / NP;
+    constexpr int G = (NP & (NP - 1)) ? 1 : 32 / NP;
     long long blocks = ((npx + G - 1) / G + kAdjWarps - 1) / kAdjWarps;
     const long long cap = (long long)device_sm_count() * 16;
     blocks = std::max<long long>(1, std::min(blocks, cap));
@@ -785,7 +787,7 @@ static cudaError_t run_adj_pixel(const float2 *C, const float *Sd, int n, long l
 template <int NP>
 static cudaError_t run_adj_uncert(const float2 *C, const float *Sd, int n, long long npx, int ref,
                                   const EmiParams &prm, float sigma2, float *out, cudaStream_t s) {
-    constexpr int G = 32 / NP;
+    constexpr int G = (NP & (NP - 1)) ? 1 : 32 / NP;
     long long blocks = ((npx + G - 1) / G + kUncWarps - 1) / kUncWarps;
     const long long cap = (long long)device_sm_count() * 32;
     blocks = std::max<long long>(1, std::min(blocks, cap));
@@ -821,6 +823,7 @@ static cudaError_t adjoint_h(const Planes &z, int n, const Geom &g, const uint64
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n <= 8) e = run_adj_pixel<8>(C, Sd, n, npx, ref, prm, dphase, H, s);
     else if (n <= 16) e = run_adj_pixel<16>(C, Sd, n, npx, ref, prm, dphase, H, s);
+    else if (n <= 24) e = run_adj_pixel<24>(C, Sd, n, npx, ref, prm, dphase, H, s);
     else e = run_adj_pixel<32>(C, Sd, n, npx, ref, prm, dphase, H, s);
     if (prof) prof->end(s);
     return e;
@@ -901,6 +904,7 @@ cudaError_t launch_phase_uncertainty(const Planes &z, int n, const Geom &g, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n <= 8) return run_adj_uncert<8>(C, Sd, n, npx, ref, prm, sigma2, sd, s);
     if (n <= 16) return run_adj_uncert<16>(C, Sd, n, npx, ref, prm, sigma2, sd, s);
+    if (n <= 24) return run_adj_uncert<24>(C, Sd, n, npx, ref, prm, sigma2, sd, s);
     return run_adj_uncert<32>(C, Sd, n, npx, ref, prm, sigma2, sd, s);
 }
 
