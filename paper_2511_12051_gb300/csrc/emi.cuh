@@ -341,18 +341,19 @@ __device__ __forceinline__ cpx<T> apply_A(const T (&g)[NP], const Loader &load, 
 // (1/(lambda - mu) for B^{-1}) and q the last convergence factor measured
 // above the noise floor.  Returns true on convergence.
 //
-// g_norm (>= ||G||_inf, 0 = none): when B for the starting shift is not
-// positive definite, the shift lies above lambda_min and the iteration would
-// converge to the eigenvalue nearest mu rather than the smallest one, so the
-// start is rebuilt once at 0.999 / g_norm, below lambda_min (lambda_min(G^-1 o C)
-// >= lambda_min(G^-1) min_i C_ii = 1 / lambda_max(G) >= 1 / ||G||_inf by Schur's
-// bound for a Hadamard product of positive semidefinite matrices), and the
-// reshifts move up from there.
+// floor_num / floor_den (floor_den > 0; 0 = none), a shift below lambda_min(A):
+// when B for the starting shift is not positive definite, the shift lies above
+// lambda_min and the iteration would converge to the eigenvalue nearest mu
+// rather than the smallest one, so the start is rebuilt once at the floor and
+// the reshifts move up from there.  For A = G^-1 o C the floor is 0.999 /
+// ||G||_inf (lambda_min(G^-1 o C) >= lambda_min(G^-1) min_i C_ii = 1 / lambda_max(G)
+// by Schur's bound for a Hadamard product of positive semidefinite matrices);
+// for A = -C it is -1.001 ||C||_inf.  The division is taken only when needed.
 template <int NP, class T, class Reform>
 __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cpx<T> &d, T &mu, T &q,
                                                   const Reform &reform, bool allow_reshift, cpx<T> *cbuf, int r,
                                                   bool live, unsigned gmask, T tol, int max_iter,
-                                                  bool build_first, T g_norm = T(0)) {
+                                                  bool build_first, T floor_num = T(0), T floor_den = T(0)) {
     const T tol2 = tol * tol;
     d = mk<T>(T(1), T(0));
     q = T(0);
@@ -374,9 +375,9 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
                 reshifts = 3;
                 pending = 2;
                 continue;
-            } else if (it == 0 && allow_reshift && !(pmin > T(0)) && g_norm > T(0)) {
+            } else if (it == 0 && allow_reshift && !(pmin > T(0)) && floor_den > T(0)) {
                 // the starting shift is above lambda_min: rebuild below it
-                mu = fmin(mu, T(0.999) / g_norm);
+                mu = fmin(mu, floor_num / floor_den);
                 continue;
             } else {
                 pending = 0;
@@ -488,7 +489,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     const bool inv_failed = clear_fail || (minpiv <= pfail) || !finite;
 
     T mu = T(prm.mu);
-    if (inv_failed) load_crow<NP, T>(a, load, r, n);  // EVD fallback: power iteration on C
+    if (inv_failed) load_crow<NP, T>(a, load, r, n);  // EVD fallback: power iteration on C first
 
     // Start vector: phases of column 0 of C (the interferograms to entry 0).
     cpx<T> x;
@@ -502,9 +503,37 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     cpx<T> d;
     T q;
     auto reform = [&](T m) { return form_shift_inverse<NP, T>(a, g, load, m, cbuf, r, n, gmask); };
-    const bool conv = inverse_iteration<NP, T>(a, x, d, mu, q, reform, !inv_failed, cbuf, r, live, gmask, tol,
-                                               prm.max_iter, !inv_failed, norm_g);
-    if (!inv_failed && conv) {
+    // Pass 0: EMI (shifted inverse iteration on A = G^-1 o C), or on the EVD
+    // fallback power iteration on C.  Power iteration converges like
+    // lambda_2 / lambda_1 = q; when that is slow its stopping rule leaves an
+    // error of about tol q / (1 - q) on the unit eigenvector, which a small entry
+    // turns into a phase error above the single-precision target, so pass 1
+    // refines by shifted inverse iteration on -C (its smallest eigenvector is the
+    // largest one of C; g = -1 makes A = g o C = -C) from a shift just below
+    // -lambda_1: rho = x^H C x <= lambda_1 and lambda_1 - lambda_2 ~ (1 - q) rho;
+    // a shift that is not below it fails the inertia check and is rebuilt at
+    // -1.001 ||C||_inf.  One call site keeps the inlined iteration single.
+    bool conv = false, refined = false, evd_power = inv_failed;
+    T fl_num = T(0.999), fl_den = norm_g;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        conv = inverse_iteration<NP, T>(a, x, d, mu, q, reform, !evd_power, cbuf, r, live, gmask, tol, prm.max_iter,
+                                        !evd_power, fl_num, fl_den);
+        if (!(evd_power && (!conv || q > T(0.3)))) break;
+        const T rho = d.x;
+        T cs = T(0);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) cs += mag_t(norm2(a[k]));  // a still holds C
+        const T cn = group_max<NP, T>(live ? cs : T(0), gmask);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) g[k] = T(-1);
+        mu = -(rho + T(0.1) * fmax(T(1) - q, T(0.01)) * rho);
+        fl_num = -T(1.001) * cn;
+        fl_den = T(1);
+        evd_power = false;
+        refined = true;
+    }
+    if (conv && (!inv_failed || refined)) {
         // Residual correction against A itself: x <- x - B^{-1} (A x - rho x).
         // Its fixed point is an exact eigenvector of A, whatever the rounding
         // of the computed B^{-1} (preconditioned inverse iteration).
@@ -516,9 +545,10 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         const T s2 = group_sum<NP, T>(norm2(xn), gmask);
         if (s2 > T(0)) x = rsqrt_t(s2) * xn;
     }
-    // x^H B^{-1} x = 1 / (lambda - mu) at convergence (EMI); x^H C x on fallback.
+    // x^H B^{-1} x = 1 / (lambda - mu) at convergence (lambda of A; -lambda_max(C)
+    // on the fallback, whose eigenvalue is not reported).
     const T theta = T(1) / ((d.x != T(0)) ? d.x : Lim<T>::tiny);
-    const T lam = inv_failed ? d.x : mu + theta;
+    const T lam = mu + theta;
 
     if (!is_fp64 && prm.fp64_resolve && !inv_failed) {
         // gap = lambda_2 - lambda_1 from q = theta / (lambda_2 - mu)
@@ -616,30 +646,25 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
     double lam = 0.0;
     bool conv = false;
     const double tol64 = 1e-9;
-    if (inv_failed) {
-        // EVD fallback, decided here in double precision: power iteration on C
-        // in single precision, as on the single-precision path (the principal
-        // eigenvector needs no more).
-        cpx<float> Cf[NP];
+    {
+        // A = G^-1 o C (EMI), or -C on the EVD fallback decided here in double
+        // precision (its smallest eigenvector is the largest one of C), with a
+        // starting shift below lambda_min(A): mu, or -1.001 ||C||_inf.
+        float mu0 = prm.mu, floor_num = 0.999f, floor_den = g_norm;
+        if (inv_failed) {
+            double cs = 0.0;
 #pragma unroll
-        for (int k = 0; k < NP; ++k) Cf[k] = mk<float>((float)A[k].x, (float)A[k].y);
-        cpx<float> xf;
-        {
-            const cpx<float> c0 = live ? Cf[0] : mk<float>(0.f, 0.f);
-            const float m2 = norm2(c0);
-            xf = (m2 > 0.f) ? (rsqrtf(m2) * c0) : mk<float>(1.f, 0.f);
-            xf = live ? (rsqrtf((float)n) * xf) : mk<float>(0.f, 0.f);
+            for (int k = 0; k < NP; ++k) cs += sqrt(norm2(A[k]));
+            const double cn = group_max<NP, double>(live ? cs : 0.0, gmask);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) A[k] = mk<double>(-A[k].x, -A[k].y);
+            mu0 = -1.001f * (float)cn;
+            floor_num = mu0;
+            floor_den = 1.f;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) A[k] = mk<double>(g[k] * A[k].x, g[k] * A[k].y);
         }
-        float mu_unused = 0.f, q_unused = 0.f;
-        cpx<float> d;
-        auto noreform = [&](float) { return 1.f; };
-        conv = inverse_iteration<NP, float>(Cf, xf, d, mu_unused, q_unused, noreform, false, fbuf, r, live, gmask,
-                                            prm.tol, prm.max_iter, false);
-        lam = d.x;
-        x64 = mk<double>((double)xf.x, (double)xf.y);
-    } else {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) A[k] = mk<double>(g[k] * A[k].x, g[k] * A[k].y);
         cpx<float> B[NP];
         auto formB = [&](float m) {
 #pragma unroll
@@ -649,7 +674,7 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
             }
             return gj_invert<NP, float, cpx<float>, false>(B, fbuf, r, n, gmask, 0.f);
         };
-        float mu = prm.mu;
+        float mu = mu0;
         cpx<float> x;
         {
             const cpx<double> c0 = live ? load(0) : mk<double>(0.0, 0.0);
@@ -661,7 +686,7 @@ __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref
         cpx<float> d;
         float q;
         inverse_iteration<NP, float>(B, x, d, mu, q, formB, true, fbuf, r, live, gmask, 1e-6f, prm.max_iter, true,
-                                     g_norm);
+                                     floor_num, floor_den);
         // Tighten the preconditioner for the double-precision phase: shift to
         // just under lambda_min (by a tenth of the gap measured through q, at
         // most half the current distance), kept only if B stays positive
