@@ -284,7 +284,7 @@ def run_batch(args, rank: int, world: int, local: int):
 
 
 def run_adjoint(args, rank: int, world: int, local: int):
-    """Adjoint workload: N=20 x 1024x1024 (cfg0-type coherence and ramp), 11x5
+    """Adjoint workload: N=20 x 1024x1024 (the 128x128 stack's coherence and ramp), 11x5
     window, stride 1, masks frozen; forward = coherence + EMI (single-precision
     solve), backward = plk_phase_link_backward of sum(w * phase), w ~ U(-1, 1);
     beside it, plk_phase_uncertainty (one adjoint solve per date and pixel) and

@@ -155,7 +155,7 @@ def config_spec(cfg: int, scale: float = 1.0, **over) -> StackSpec:
         p0y, p0x, pn = int(924 * scale), int(1948 * scale), max(1, int(200 * scale))
         s = StackSpec(N=60, H=H, W=W, rho0=0.7, rho_inf=0.1, tau=48.0,
                       step=(30, p0y, p0y + pn, p0x, p0x + pn, 2.0), seed=3)
-    elif cfg == 4:  # N=20 x 1024x1024, config-0 coherence and ramp
+    elif cfg == 4:  # N=20 x 1024x1024, coherence and ramp of the 128x128 stack
         s = StackSpec(N=20, H=sz(1024), W=sz(1024), rho0=0.7, rho_inf=0.1, tau=48.0, seed=4)
     else:
         raise ValueError(f"unknown workload {cfg}")

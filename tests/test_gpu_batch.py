@@ -30,7 +30,7 @@ def ctx(plk):
     return plk.Context("cuda:0")
 
 
-def cfg2_stack(N, seed, H=48, W=120, rho0=0.6):
+def uneven_stack(N, seed, H=48, W=120, rho0=0.6):
     # one stack of the uneven-batch workload, scaled down; 5% of the pixels in
     # 8 x 8 patches of coherence 0.98 (near-singular |Gamma|)
     spec = synth.config_spec(2, N=N, H=H, W=W, seed=seed, rho0=rho0, patches=(0.05, 8, 0.98))
@@ -50,7 +50,7 @@ def test_batch_uneven_stacks_match_oracle(ctx, plk):
     Ns = [5, 9, 15, 17, 24, 30]
     refs = [0, 3, 0, 16, 5, 29]
     rhos = [0.3, 0.9, 0.6, 0.45, 0.75, 0.5]
-    zs = [cfg2_stack(N, 100 + i, rho0=r) for i, (N, r) in enumerate(zip(Ns, rhos))]
+    zs = [uneven_stack(N, 100 + i, rho0=r) for i, (N, r) in enumerate(zip(Ns, rhos))]
     b = plk.Batch(ctx, [z.cuda() for z in zs], WIN, refs=refs)
     out = b.run()
     torch.cuda.synchronize()
@@ -75,7 +75,7 @@ def test_batch_uneven_stacks_match_oracle(ctx, plk):
 
 def test_batch_equals_single_stack_path_and_replays(ctx, plk):
     Ns = [6, 15, 21]
-    zs = [cfg2_stack(N, 200 + N, H=60, W=150).cuda() for N in Ns]
+    zs = [uneven_stack(N, 200 + N, H=60, W=150).cuda() for N in Ns]
     b = plk.Batch(ctx, zs, WIN)
     first = [{k: v.clone() for k, v in o.items()} for o in b.run()]
     torch.cuda.synchronize()

@@ -133,7 +133,7 @@ def test_phase_link_without_fp64_resolve(plk, ctx, cfg, N, ref):
     o = oracle.phase_link(C32.astype(np.complex128), N, ref)
     clear = same & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
     assert phase_report(to_np(s["phase"]), o["phase"], clear)["max"] <= PHASE_TOL
-    print(f"cfg{cfg}: {np.sum(st_d == 1)} pixels re-solved in double precision by default, "
+    print(f"workload {cfg}: {np.sum(st_d == 1)} pixels re-solved in double precision by default, "
           f"statuses without: {np.bincount(st_s.ravel(), minlength=5).tolist()}")
 
 
@@ -171,17 +171,17 @@ def test_compress_parity(ctx, win, first_real, N, W):
 # ------------------------------------------------------------- S1-S8 chain
 
 def chain_case(case):
-    if case == "cfg0":
+    if case == "n10_128px":
         z, spec = stack(0, H=72, W=90)
         return z, (5, 11, 1, 1), 10, 6, 10
-    if case == "cfg1":
+    if case == "burst_n15":
         z, spec = stack(1, H=96, W=300)
         return z, (5, 11, 3, 6), 15, 6, 15
     z, spec = stack(3, scale=0.05)  # 60 dates, 102 x 205, step patch inside
     return z, (5, 11, 1, 1), 15, 3, 60
 
 
-@pytest.mark.parametrize("case", ["cfg0", "cfg1", "cfg3"])
+@pytest.mark.parametrize("case", ["n10_128px", "burst_n15", "chain_60d"])
 def test_ministack_step_parity(plk, ctx, case, tmp_path):
     """Each step from identical inputs: the oracle's state (compressed SLCs as
     stored complex64 samples, power sums) is loaded into the library through its
@@ -215,7 +215,7 @@ def test_ministack_step_parity(plk, ctx, case, tmp_path):
         st.close()
 
 
-@pytest.mark.parametrize("case", ["cfg1", "cfg3"])
+@pytest.mark.parametrize("case", ["burst_n15", "chain_60d"])
 def test_ministack_chain_end_to_end(plk, ctx, case):
     """The whole chain, each side carrying its own compressed SLCs: single-
     precision differences in kappa propagate, so the bar is statistical
@@ -289,7 +289,7 @@ def test_edge_cases(plk, ctx):
         ctx.phase_link(torch.zeros((4, 3), dtype=torch.complex64, device="cuda"), 2, 5)
 
 
-@pytest.mark.parametrize("case", ["cfg1", "cfg3"])
+@pytest.mark.parametrize("case", ["burst_n15", "chain_60d"])
 def test_ministack_step_parity_last_real_scheme(plk, ctx, case, tmp_path):
     """The production reference scheme (each compressed SLC carries its
     mini-stack's last real date): every step from identical inputs against the
