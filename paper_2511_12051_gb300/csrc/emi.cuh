@@ -17,8 +17,9 @@
 //   v   = lim x_{t+1} = B^{-1} x_t / |B^{-1} x_t| (inverse iteration with
 //         shift mu = 0.99, Sec. III-B), started from the phases of column 0
 //         of C.
-//   EVD fallback where G is not invertible: power iteration on C (largest
-//         eigenvector, Sec. III-B).
+//   EVD fallback where G is not invertible: the largest eigenvector of C
+//         (Sec. III-B), by power iteration, refined by shifted inverse
+//         iteration on -C when that converges slowly.
 #pragma once
 
 #include "cpx.cuh"
@@ -612,8 +613,9 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
 // double precision until the correction vanishes, so the fixed point is an
 // eigenvector of the double-precision A (preconditioned inverse iteration).
 // The inversion of G fails (EVD fallback) when a double-precision pivot is <=
-// kPivotFail; the decision is the double-precision one, the power iteration
-// on C then runs in single precision, as do the reference phase and gamma_t.
+// kPivotFail; the decision is the double-precision one, and the same
+// preconditioned iteration then runs on A = -C (its smallest eigenvector is the
+// largest one of C); the reference phase and gamma_t run in single precision.
 template <int NP, class Loader>
 __device__ PixelResult emi_solve_mixed(const Loader &load, int r, int n, int ref, const EmiParams &prm,
                                        cpx<double> *dbuf, unsigned gmask, int glane0) {
