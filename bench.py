@@ -177,6 +177,8 @@ def run_reference(args, rank: int):
     spec.H = 512
     z = synth.generate(spec, device="cpu")
     per_step_target = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    if args.ref_step_seconds is not None:
+        per_step_target = args.ref_step_seconds
     rows, cols, _ = size_cpu_sample(z, per_step_target)
     rows = min(rows, spec.H - spec.H % WINDOW[2])
     crop = cpu_crop(z, rows, cols)
@@ -478,6 +480,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=None,
+                    help="CPU seconds of oracle work per step of the reference arm (default: 2-20 s, "
+                         "so that the whole run takes a few minutes)")
     ap.add_argument("--rows", type=int, default=H_FULL, help="image rows (smaller cases for profiling only)")
     ap.add_argument("--cols", type=int, default=W_FULL, help="image columns (smaller cases for profiling only)")
     ap.add_argument("--cov-precision", default="fp32", choices=["fp32", "bf16", "fp16"],
