@@ -69,7 +69,10 @@ typedef struct plk_params {
     double alpha;      /* GLRT size (Sec. III-A), 0 < alpha < 1; default 1e-3 */
     float beta;        /* |C| regularisation G = (1-beta)|C| + beta I, 0 <= beta < 1;
                           default 0, the paper's plug-in |C| (Sec. III-B) */
-    float mu;          /* inverse-iteration shift (Sec. III-B); default 0.99 */
+    float mu;          /* starting inverse-iteration shift (Sec. III-B); default
+                          0.99.  A shift at or above lambda_min (its B is not
+                          positive definite) is replaced by 0.999/||G||_inf, a
+                          lower bound, and moved up by the reshifts */
     float tol;         /* stop when the unit iterate moves less than tol (2-norm,
                           after removing a common phase); default 1e-6 */
     int32_t max_iter;  /* inverse-iteration cap, all shifts together; default 100 */
