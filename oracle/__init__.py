@@ -241,4 +241,5 @@ from .chain import OracleChain, ministack  # noqa: E402,F401
 from .similarity import disk_offsets, nearest3_pairs, phase_similarity  # noqa: E402,F401
 from .inversion import incidence, l1_invert, soft_threshold  # noqa: E402,F401
 from .weights import mask_weights, weighted_coherence, window_samples  # noqa: E402,F401
-from .decay import decay_weights, effective_looks, glrt_threshold_real, merge_group, merged_mean_variance  # noqa: E402,F401
+from .decay import (decay_weights, effective_looks, glrt_threshold_real, merge_group, merge_group_f32,  # noqa: E402,F401
+                    merged_mean_variance, step_weights, weight_sums)

@@ -32,15 +32,18 @@ from __future__ import annotations
 import numpy as np
 
 from . import amp_stats, compress, covariance, glrt_threshold, ntri, phase_link, ps_compress, ps_regrid, shp_select
+from .decay import glrt_threshold_real, merge_group_f32, weight_sums
 
 
 def ministack(z: np.ndarray, first_real: int, window, sum_pow: np.ndarray, n_eff: int,
               alpha: float, ref: int, beta: float = 0.0, cond: bool = False, scheme: str = "first",
-              sum_amp: np.ndarray | None = None, ps_da_max: float = 0.0) -> dict:
+              sum_amp: np.ndarray | None = None, ps_da_max: float = 0.0, c: float | None = None) -> dict:
     """One mini-stack through S2-S7 with statistics already merged (PS
-    regridding of the returned phases when ps_da_max > 0)."""
+    regridding of the returned phases when ps_da_max > 0).  c: the GLRT
+    threshold, when it is not the one for n_eff looks (decaying weights)."""
     N = z.shape[0]
-    c = glrt_threshold(alpha, n_eff)
+    if c is None:
+        c = glrt_threshold(alpha, n_eff)
     mask, count = shp_select(sum_pow, window, np.float32(c))
     C = covariance(z, window, mask)
     out = phase_link(C, N, ref, beta, cond=cond)
@@ -66,8 +69,14 @@ class OracleChain:
     """Sequential processing state: kappa ring, merged power sums, image count."""
 
     def __init__(self, H: int, W: int, window, K_max: int, alpha: float = 1e-3, beta: float = 0.0,
-                 kappa_dtype=np.complex128, scheme: str = "first", ps_da_max: float = 0.0):
+                 kappa_dtype=np.complex128, scheme: str = "first", ps_da_max: float = 0.0, decay: float = 1.0):
         assert scheme in ("first", "last")
+        # decay < 1: step 1 merges with exponentially decaying image weights
+        # (oracle/decay.py, single-precision sums in the decision order) and
+        # step 2 takes nu = W1^2 / W2 effective looks.
+        assert 0.0 < decay <= 1.0 and (decay == 1.0 or ps_da_max == 0.0)
+        self.decay = decay
+        self.wsum = None  # (W1, W2): sums of the image weights and of their squares
         self.scheme = scheme
         self.ps_da_max = ps_da_max
         # kappa_dtype=np.complex64 stores each compressed SLC rounded to the
@@ -86,7 +95,15 @@ class OracleChain:
     def step(self, new_slc: np.ndarray, cond: bool = False) -> dict:
         new_slc = np.ascontiguousarray(new_slc, dtype=np.complex64)
         M = new_slc.shape[0]
-        amp_stats(new_slc, self.sum_pow, self.sum_amp, accumulate=True)
+        c = None
+        if self.decay == 1.0:
+            amp_stats(new_slc, self.sum_pow, self.sum_amp, accumulate=True)
+        else:
+            first = self.n == 0
+            self.sum_pow, self.sum_amp = merge_group_f32(None if first else self.sum_pow,
+                                                         None if first else self.sum_amp, new_slc, self.decay)
+            self.wsum = weight_sums(None if first else self.wsum, M, self.decay)
+            c = glrt_threshold_real(self.alpha, max(1.0, self.wsum[0] ** 2 / self.wsum[1]))
         self.n += M
         K = len(self.ring)
         parts = [np.stack(self.ring).astype(np.complex128)] if K else []
@@ -94,7 +111,7 @@ class OracleChain:
         z = np.concatenate(parts, axis=0)
         ref = K - 1 if K > 0 else 0
         out = ministack(z, K, self.window, self.sum_pow, self.n, self.alpha, ref, self.beta, cond, self.scheme,
-                        self.sum_amp, self.ps_da_max)
+                        self.sum_amp, self.ps_da_max, c)
         self.ring.append(out["kappa"].astype(self.kappa_dtype).astype(np.complex128))
         if len(self.ring) > self.K_max:
             self.ring.pop(0)

@@ -58,6 +58,56 @@ def effective_looks(state: dict) -> float:
     return state["W1"] ** 2 / state["W2"]
 
 
+def step_weights(M: int, lam: float) -> tuple[np.ndarray, np.float32]:
+    """The weights of one merge in single precision: w_j = lam^(M - 1 - j)
+    for the group's images j = 0..M-1 and s = lam^M for the running sums,
+    each a product of lam's formed in double precision (w_{M-1} = 1, w_{j-1} =
+    w_j lam, s = w_0 lam) and rounded once to single precision."""
+    w = np.empty(M, np.float64)
+    acc = 1.0
+    for j in range(M - 1, -1, -1):
+        w[j] = acc
+        acc *= lam
+    return w.astype(np.float32), np.float32(acc)
+
+
+def merge_group_f32(sum_pow: np.ndarray | None, sum_amp: np.ndarray | None, group: np.ndarray, lam: float):
+    """merge_group's sums P and A in single precision, in the fixed order the
+    GLRT decision is taken in on both sides of the parity test (the paper
+    fixes no precision for it): per pixel, q_j = fl(fl(x^2) + fl(y^2)) and
+    P_g = sum_j fl(w_j q_j), A_g = sum_j fl(w_j sqrt(q_j)), j ascending from 0;
+    then P = fl(fl(s P_old) + P_g), A likewise (P = P_g on a first group).  With
+    lam = 1 every weight is 1 and this is the equal-weight sum of amp_stats.
+    Returns new float32 arrays."""
+    z = np.asarray(group, dtype=np.complex64)
+    M = z.shape[0]
+    w, s = step_weights(M, lam)
+    Pg = np.zeros(z.shape[1:], np.float32)
+    Ag = np.zeros(z.shape[1:], np.float32)
+    for j in range(M):
+        x, y = z[j].real.astype(np.float32), z[j].imag.astype(np.float32)
+        q = (x * x) + (y * y)
+        Pg = Pg + w[j] * q
+        Ag = Ag + w[j] * np.sqrt(q)
+    if sum_pow is None:
+        return Pg, Ag
+    return (s * np.asarray(sum_pow, np.float32)) + Pg, (s * np.asarray(sum_amp, np.float32)) + Ag
+
+
+def weight_sums(prev: tuple[float, float] | None, M: int, lam: float) -> tuple[float, float]:
+    """W1 = sum of weights and W2 = sum of squared weights after merging a
+    group of M images into running sums (W1, W2) (None: the first group), in
+    double precision with the same single-precision weights as the sums."""
+    w, s = step_weights(M, lam)
+    w1 = float(np.sum(w.astype(np.float64)))
+    w2 = float(np.sum(w.astype(np.float64) ** 2))
+    if prev is None:
+        return w1, w2
+    W1, W2 = prev
+    sd = float(s)
+    return sd * W1 + w1, sd * sd * W2 + w2
+
+
 def glrt_threshold_real(alpha: float, nu: float) -> float:
     """c = F^{-1}_{2 nu, 2 nu}(1 - alpha / 2) for a real number of looks."""
     return float(scipy.stats.f.ppf(1.0 - alpha / 2.0, 2.0 * nu, 2.0 * nu))

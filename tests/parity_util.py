@@ -34,14 +34,18 @@ def phase_report(gpu_phase, orc_phase, valid=None):
 
 def write_state_file(path, chain, M_max=None):
     """Write an oracle chain's state in the library's checkpoint format
-    (magic, int32 header, ring oldest..newest as complex64, power and
-    amplitude sums as float32)."""
+    (magic, int32 header, for format 2 the weight sums W1, W2 as float64, ring
+    oldest..newest as complex64, power and amplitude sums as float32).  Format
+    1 (equal weights) unless the chain decays its image weights."""
     H, W = chain.H, chain.W
     wy, wx, sy, sx = chain.window
     hdr = np.array([H, W, wy, wx, sy, sx, chain.K_max, len(chain.ring), chain.n, 0], np.int32)
+    decaying = getattr(chain, "decay", 1.0) != 1.0
     with open(path, "wb") as f:
-        f.write(b"PLKSTAT1")
+        f.write(b"PLKSTAT2" if decaying else b"PLKSTAT1")
         f.write(hdr.tobytes())
+        if decaying:
+            f.write(np.array(chain.wsum if chain.wsum is not None else (0.0, 0.0), np.float64).tobytes())
         for k in chain.ring:
             f.write(np.ascontiguousarray(k, np.complex64).tobytes())
         f.write(np.ascontiguousarray(chain.sum_pow, np.float32).tobytes())

@@ -75,3 +75,44 @@ def test_weights_and_effective_looks_limits():
 def test_real_threshold_matches_the_integer_bisection(n):
     assert oracle.glrt_threshold_real(1e-3, n) == pytest.approx(oracle.glrt_threshold(1e-3, n), rel=1e-8)
     assert oracle.glrt_threshold_real(1e-3, n + 0.5) < oracle.glrt_threshold_real(1e-3, n)
+
+
+# ------------------------------------------------ single-precision decision sums
+
+def test_f32_sums_at_equal_weights_are_the_plain_sums_bit_for_bit():
+    """lam = 1: every weight is exactly 1, so the decision-precision merge is
+    the C oracle's equal-weight accumulation, bit for bit."""
+    groups = [stack(5, seed=11), stack(2, seed=12), stack(9, seed=13)]
+    P = A = None
+    sp = sa = None
+    for i, g in enumerate(groups):
+        P, A = oracle.merge_group_f32(P, A, g, 1.0)
+        sp, sa = oracle.amp_stats(g, sp, sa, accumulate=i > 0)
+    assert P.dtype == np.float32 and np.array_equal(P, sp) and np.array_equal(A, sa)
+
+
+@pytest.mark.parametrize("lam", [0.5, 0.9, 0.97])
+def test_f32_sums_follow_the_double_sums(lam):
+    groups = [stack(6, seed=14), stack(3, seed=15), stack(4, seed=16)]
+    st = None
+    P = A = None
+    for g in groups:
+        st = oracle.merge_group(st, g, lam)
+        P, A = oracle.merge_group_f32(P, A, g, lam)
+    np.testing.assert_allclose(P, st["P"], rtol=2e-6)
+    np.testing.assert_allclose(A, st["A"], rtol=2e-6)
+
+
+@pytest.mark.parametrize("lam", [0.6, 0.95, 1.0])
+def test_weight_sums_and_step_weights(lam):
+    w, s = oracle.step_weights(5, lam)
+    assert w[-1] == 1.0 and w.dtype == np.float32
+    np.testing.assert_allclose(w[:-1] / w[1:], lam, rtol=1e-6)
+    assert s == pytest.approx(lam ** 5, rel=1e-6)
+    st, ws = None, None
+    for M in (4, 7, 2):
+        st = oracle.merge_group(st, stack(M, seed=M), lam)
+        ws = oracle.weight_sums(ws, M, lam)
+    assert ws[0] == pytest.approx(st["W1"], rel=1e-6) and ws[1] == pytest.approx(st["W2"], rel=1e-6)
+    if lam == 1.0:
+        assert ws == (13.0, 13.0)
