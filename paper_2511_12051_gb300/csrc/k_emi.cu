@@ -67,6 +67,27 @@ struct EmiMinBlocks {
     static constexpr int value = NP == 32 ? 1 : (NP == 24 ? 3 : PLK_EMI_MINB);
 };
 
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (the
+// source is then not read but must be a valid pointer).
+__device__ __forceinline__ void cp_async8_emi(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Prefetch depth of the packed coherences: the warp copies the triangles of
+// its next G pixels (G * N(N+1)/2 entries, one contiguous run) into shared
+// memory while it solves the current ones, so the gather of a pixel's rows
+// reads shared memory instead of waiting on global loads.  Off for 32-entry
+// rows, whose two buffers would exceed the static shared-memory budget.
+template <int NP>
+struct EmiPrefetch {
+    static constexpr int G = ((NP & (NP - 1)) == 0) ? 32 / NP : 1;
+    static constexpr bool on = NP <= 24;
+    static constexpr int elems = on ? G * NP * (NP + 1) / 2 : 1;
+};
+
 template <int NP>
 __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi32(const float2 *__restrict__ C, int n, long long npx,
                                                           int ref, const EmiParams prm,
@@ -74,11 +95,13 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
                                                           float *__restrict__ lam, uint8_t *__restrict__ status) {
     constexpr bool kPow2 = (NP & (NP - 1)) == 0;
     constexpr int G = kPow2 ? 32 / NP : 1;
+    constexpr bool kPf = EmiPrefetch<NP>::on;
     // Complex entries per cached row: NP + 2 (16-byte aligned rows whose
     // 16-byte chunks fall in different banks for 8 consecutive lanes).
     constexpr int kRowPitch = NP + 2;
     __shared__ __align__(16) cpx<float> sbuf[kEmiWarps][32];
     __shared__ __align__(16) cpx<float> rowcache[kEmiWarps * 32 * kRowPitch];
+    __shared__ __align__(16) float2 pf[kEmiWarps][kPf ? 2 : 1][EmiPrefetch<NP>::elems];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
@@ -87,12 +110,36 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
     const long long step = (long long)gridDim.x * kEmiWarps * G;
     cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
 
-    for (long long base = ((long long)blockIdx.x * kEmiWarps + warp) * G; base < npx; base += step) {
+    // Copy the packed triangles of pixels b .. b + G - 1 (those below npx)
+    // into prefetch slot `slot`; one commit group per call, empty past the end.
+    auto prefetch = [&](long long b, int slot) {
+        if constexpr (kPf) {
+            const long long cnt = b < npx ? ((npx - b < G) ? (npx - b) : G) * nt : 0;
+            const float2 *src = C + (b < npx ? b : 0) * nt;
+            for (int e = lane; e < G * nt; e += 32) {
+                const bool ok = e < cnt;
+                cp_async8_emi(&pf[warp][slot][e], ok ? src + e : C, ok ? 8 : 0);
+            }
+            cp_async_commit();
+        }
+    };
+    long long base = ((long long)blockIdx.x * kEmiWarps + warp) * G;
+    int slot = 0;
+    prefetch(base, 0);
+    for (; base < npx; base += step, slot ^= 1) {
         const long long p = base + grp;
         const bool valid = p < npx;
-        const float2 *Cpix = C + (valid ? p : 0) * nt;
+        const float2 *Cpix;
+        if constexpr (kPf) {
+            prefetch(base + step, slot ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");  // this iteration's copies have landed
+            __syncwarp();
+            Cpix = &pf[warp][slot][grp * nt];
+        } else {
+            Cpix = C + (valid ? p : 0) * nt;
+        }
         bool nan = false;
-        if (valid && r < n) nan = isnan(__ldg(Cpix + packed_index(n, r, r)).x);
+        if (valid && r < n) nan = isnan(Cpix[packed_index(n, r, r)].x);
         nan = __any_sync(gmask, nan);
         if (valid && !nan) {
             // Gather row r once: entries k >= r are contiguous in the packed
@@ -106,10 +153,10 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
                     v[k] = mk<float>((r >= n && k == r) ? 1.f : 0.f, 0.f);
                     if (r < n && k < n) {
                         if (k >= r) {
-                            const float2 c = __ldg(Cpix + base_r + k);
+                            const float2 c = Cpix[base_r + k];
                             v[k] = mk<float>(c.x, c.y);
                         } else {
-                            const float2 c = __ldg(Cpix + idx_col);
+                            const float2 c = Cpix[idx_col];
                             v[k] = mk<float>(c.x, -c.y);
                             idx_col += n - k - 1;
                         }
@@ -143,8 +190,9 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
                 status[p] = PLK_PX_NODATA;
             }
         }
-        __syncwarp();
+        __syncwarp();  // the slot is free for the copies issued next iteration
     }
+    if constexpr (kPf) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Double-precision re-solve of the pixels left pending.  Each warp scans 32
@@ -202,11 +250,33 @@ struct RegRow {
     __device__ __forceinline__ cpx<T> operator()(int k) const { return c[k]; }
 };
 
+// Sum of exact products in a pair of floats (hi + lo): the product a*b is
+// split exactly into p + e (p = fl(a*b), e = fma(a, b, -p)), and p is added to
+// hi by Knuth's TwoSum, its rounding error going to lo with e.  The
+// intrinsics keep the compiler from contracting or reordering any step.  Over
+// the few dozen looks of a window the pair carries about 46 significant bits,
+// as a double-precision sum of the same products does (each product of two
+// single-precision samples is exact in double precision); GB300's FP32 pipes
+// do this several times faster than its FP64 units do the double sum.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ void f2_add_prod(F2 &acc, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ double f2_value(const F2 &a) { return (double)a.hi + (double)a.lo; }
+
 // Double-precision re-solve for the mini-stack path: the coherence row of a
-// pending pixel is recomputed from the SLC stack over its SHP neighbourhood,
-// in double precision (products of single-precision samples are exact in
-// double), so the solve sees the same coherence as an FP64 reference instead
-// of the single-precision one.
+// pending pixel is recomputed from the SLC stack over its SHP neighbourhood
+// with exact products and float-pair sums (F2), carried to double precision,
+// so the solve sees the coherence an FP64 reference computes instead of the
+// single-precision one.
 template <int NP>
 __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_constant__ Planes z, const Geom g,
                                                                 const uint64_t *__restrict__ mask, int n,
@@ -243,9 +313,9 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
                 const int oy = (int)(p / g.Wo), ox = (int)(p - (p / g.Wo) * g.Wo);
                 const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
                 const uint64_t *mw = mask + p * g.nwords;
-                RegRow<NP, double> row;
+                F2 re[NP], im[NP];
 #pragma unroll
-                for (int k = 0; k < NP; ++k) row.c[k] = mk<double>(0.0, 0.0);
+                for (int k = 0; k < NP; ++k) re[k] = im[k] = F2{0.f, 0.f};
                 int b = 0;
                 uint64_t word = __ldg(mw);
                 for (int dy = -g.hy; dy <= g.hy; ++dy)
@@ -255,17 +325,21 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
                         const long long q = (long long)(cy + dy) * g.W + (cx + dx);
                         float2 zr = make_float2(0.f, 0.f);
                         if (r < n) zr = __ldg(z.p[r] + q);
-                        const double xr = zr.x, yr = zr.y;
 #pragma unroll
                         for (int k = 0; k < NP; ++k) {
                             if (k < n) {
                                 const float2 zk = __ldg(z.p[k] + q);
-                                const double xk = zk.x, yk = zk.y;
-                                row.c[k].x += xr * xk + yr * yk;
-                                row.c[k].y += yr * xk - xr * yk;
+                                // z_r conj(z_k) = (xr xk + yr yk) + j (yr xk - xr yk)
+                                f2_add_prod(re[k], zr.x, zk.x);
+                                f2_add_prod(re[k], zr.y, zk.y);
+                                f2_add_prod(im[k], zr.y, zk.x);
+                                f2_add_prod(im[k], -zr.x, zk.y);
                             }
                         }
                     }
+                RegRow<NP, double> row;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) row.c[k] = mk<double>(f2_value(re[k]), f2_value(im[k]));
                 // normalise: C_rk = S_rk s_r s_k with s_i = 1/sqrt(S_ii) (0 when
                 // S_ii = 0), C_rr = 1; one square root per lane.
                 cpx<double> *buf = &sbuf[warp][glane0];
