@@ -632,6 +632,8 @@ def main():
         bi = zh.numel() * zh.element_size()
         bo = sum(v.numel() * v.element_size() for v in oh.values() if v is not None)
 
+        st.enable_host_io()
+
         def e2e_step():
             st.reset()
             st.step_host(zh, params, out=oh)

@@ -55,7 +55,8 @@ enum {
     PLK_PX_EMI_FP64 = 1,  /* EMI solution re-solved in double precision */
     PLK_PX_EVD = 2,       /* inversion of |C| failed: EVD fallback (Sec. III-B) */
     PLK_PX_NODATA = 3,    /* zero-power centre / empty neighbourhood: NaN outputs */
-    PLK_PX_NOCONV = 4,    /* inverse iteration hit max_iter; last iterate kept */
+    PLK_PX_NOCONV = 4,    /* inverse iteration (EMI or EVD fallback) hit max_iter;
+                             last iterate kept */
     PLK_PX_PS = 5         /* output cell takes the phase of a persistent scatterer
                              (plk_ps_regrid, Supplement "Regridding PS and DS") */
 };
@@ -75,7 +76,9 @@ typedef struct plk_params {
                           lower bound, and moved up by the reshifts */
     float tol;         /* stop when the unit iterate moves less than tol (2-norm,
                           after removing a common phase); default 1e-6 */
-    int32_t max_iter;  /* inverse-iteration cap, all shifts together; default 100 */
+    int32_t max_iter;  /* inverse-iteration cap, all shifts together (on the EVD
+                          fallback, the power iteration and its refinement
+                          together); default 100 */
     float cond_max;    /* pixels whose 1-norm condition number of G exceeds
                           cond_max, or whose single-precision inversion of G meets
                           a pivot within 2e-5 of the 1e-4 failure limit, are
@@ -102,6 +105,20 @@ typedef struct plk_params {
                               arg(z_i conj z_ref), so that later mini-stacks keep
                               its datum; default 0 (off); the paper's production
                               value is 0.2 */
+    float decay;           /* plk_ministack_step: weighting of the merged
+                              amplitude statistics (Sec. III-A, the exponential
+                              decay option beside equal weights per image):
+                              image t of the T merged so far weighs
+                              decay^(T-1-t), the newest 1.  0 < decay <= 1;
+                              default 1 (equal weights, the sums of
+                              plk_amp_stats).  Below 1, S1 keeps decayed sums
+                              (each image's power times its weight, in single
+                              precision, images in order; the running sums
+                              scaled by decay^M before a group of M is added)
+                              and the GLRT uses nu = W1^2 / W2 effective looks
+                              (W1, W2: sums of the weights and of their
+                              squares) through plk_glrt_threshold_looks.  Not
+                              with ps_da_max > 0 (EUNSUPPORTED) */
 } plk_params;
 
 /* Mini-stack reference schemes (plk_params.ref_scheme).  Both link each
@@ -171,6 +188,11 @@ plk_status plk_profile_get(const plk_ctx *ctx, int i, const char **name, double 
  * size-alpha GLRT accepts iff max/min <= c = F^{-1}_{2n,2n}(1 - alpha/2).
  * Writes c to *c (host pointer).  EINVAL if alpha not in (0,1) or n_eff < 1. */
 plk_status plk_glrt_threshold(double alpha, int n_eff, double *c);
+/* The same threshold for a real number of looks nu >= 1 (Sec. III-A with
+ * exponentially decaying image weights, nu = W1^2 / W2): the ratio of two
+ * weighted power sums is taken as F(2 nu, 2 nu) distributed.  Equals
+ * plk_glrt_threshold at integer nu.  EINVAL if alpha not in (0,1) or nu < 1. */
+plk_status plk_glrt_threshold_looks(double alpha, double nu, double *c);
 
 /* ---------------------------------------------------------- hot-path calls */
 
@@ -180,7 +202,10 @@ plk_status plk_glrt_threshold(double alpha, int n_eff, double *c);
  * single precision, no fused multiply-add (the sums decide mask bits).
  * accumulate = 0: sum_pow = P (and sum_amp = A); accumulate = 1: sum_pow +=
  * P (one float add), which merges a new group into the running statistics.
- * sum_pow [H][W] float is required; sum_amp may be NULL.  n >= 1. */
+ * sum_pow [H][W] float is required; sum_amp may be NULL.  n >= 1.
+ * The sums are float, not double: the GLRT decision is taken in single
+ * precision on both sides of the parity test, in a fixed order of operations,
+ * so masks match bit for bit (the paper fixes no precision for it). */
 plk_status plk_amp_stats(plk_ctx *ctx, const plk_c64 *slc, int n, int H, int W,
                          float *sum_pow, float *sum_amp, int accumulate);
 
@@ -190,7 +215,8 @@ plk_status plk_amp_stats(plk_ctx *ctx, const plk_c64 *slc, int n, int H, int W,
  * neighbour q is inside the image, P_p > 0, P_q > 0 and
  *   max(P_p, P_q) <= fl(c * min(P_p, P_q)),  c = (float) plk_glrt_threshold.
  * mask is [Ho][Wo][plk_mask_words(win)] uint64; count [Ho][Wo] uint16 gets the
- * number of set bits (the paper's shp_counts layer; 0 marks no-data). */
+ * number of set bits (the paper's shp_counts layer; 0 marks no-data).
+ * sum_pow is float, as plk_amp_stats writes it (single-precision decision). */
 plk_status plk_shp_select(plk_ctx *ctx, const float *sum_pow, int n_eff, int H, int W,
                           plk_window win, double alpha, uint64_t *mask, uint16_t *count);
 
@@ -251,6 +277,9 @@ plk_status plk_state_destroy(plk_state *st);
 plk_status plk_state_reset(plk_state *st);
 /* Host-side counters: compressed SLCs held, real images merged, steps run. */
 plk_status plk_state_info(const plk_state *st, int *K_used, int *n_eff, int *steps);
+/* Sums of the image weights merged so far and of their squares (W1, W2;
+ * both n_eff with equal weights); nu = W1^2 / W2 effective looks. */
+plk_status plk_state_weights(const plk_state *st, double *W1, double *W2);
 /* Device pointer to compressed SLC i of the ring (0 = oldest), [H][W]. */
 plk_status plk_state_kappa(const plk_state *st, int i, const plk_c64 **kappa);
 /* Device pointers to the merged sums [H][W] (sum_amp may be NULL). */
@@ -285,10 +314,20 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
  * until plk_sync(ctx).  The SLCs go to one of two device staging buffers on a
  * copy stream of the library's own, so a call's copy overlaps the previous
  * call's compute (with pinned host memory; pageable memory works but copies
- * synchronously).  The first call allocates the two staging buffers (M_max
- * planes each) and the device outputs; plk_state_destroy releases them.
- * Errors: EINVAL, ENOMEM, ECUDA, and those of plk_ministack_step.  Not part
- * of the paper's method: a transfer schedule around it. */
+ * synchronously).  The staging buffers come from plk_state_enable_host_io,
+ * which must have been called on st (EINVAL otherwise); the step itself
+ * allocates nothing.  Errors: EINVAL, ECUDA, and those of plk_ministack_step.
+ * Not part of the paper's method: a transfer schedule around it. */
+/* Set-up for plk_ministack_step_host: allocates st's two device staging
+ * buffers (M_max planes of H x W each), the device outputs, a copy stream and
+ * its events; plk_state_destroy releases them.  A second call does nothing.
+ * Errors: EINVAL, ENOMEM (nothing is kept). */
+plk_status plk_state_enable_host_io(plk_ctx *ctx, plk_state *st);
+/* Device allocations (successful cudaMalloc calls) the library has made in
+ * this process: contexts, states, host-I/O staging, batches.  A diagnostic for
+ * callers that must not allocate after set-up; no step or hot-path call adds
+ * to it. */
+int64_t plk_device_allocations(void);
 plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
                                    const plk_params *params, float *phase, float *tcoh, uint8_t *status,
                                    uint16_t *shp_count);
@@ -463,7 +502,11 @@ plk_status plk_tuned_schedule(const plk_ctx *ctx, int N, plk_window win, int *co
  * inside a host application that owns every device allocation, or a service
  * that must not allocate after start-up.  Outputs as plk_phase_link:
  * phase [N][Ho][Wo], tcoh and status [Ho][Wo]; shp_count [Ho][Wo] may be NULL.
- * Results equal those of plk_ministack_step on a fresh state (ref_idx = 0).
+ * Results equal those of plk_ministack_step on a fresh state (ref_idx = 0)
+ * with the same params; coherence in FP32, BF16 or FP16 (params->cov_precision,
+ * N <= 32 for the last two).  Persistent-scatterer regridding
+ * (params->ps_da_max > 0) is not run here: EUNSUPPORTED.  params are checked
+ * as by the other entry points (EINVAL).
  * Work is issued on cuda_stream on the CURRENT device.
  * Scratch: sums, masks, counts and coherence live in a file-scope device array
  * of PLK_NOALLOC_SCRATCH_BYTES shared by every call; inputs and outputs stay
@@ -472,8 +515,10 @@ plk_status plk_tuned_schedule(const plk_ctx *ctx, int N, plk_window win, int *co
  * plk_last_error(NULL).  Every scratch region is written in full before it is
  * read within a call, so nothing needs clearing; calls that overlap on the
  * GPU (other streams, other threads) race on the shared array and must be
- * serialized by the caller.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and keeps it; make that first call
+ * serialized by the caller.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device, so the address is right even
+ * after that device's context was reset and made again; the first call on a
+ * device also loads the library's device code there, so make that first call
  * before any stream capture.  Errors: EINVAL (bad argument, too large),
  * EUNSUPPORTED, ECUDA; text in plk_last_error(NULL). */
 plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, int H, int W, plk_window win,

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "api_internal.h"
@@ -16,6 +17,7 @@ struct plk_state {
     plk_window win;
     int K_max, M_max;
     int K_used, n_eff, steps, head;
+    double W1, W2;       // sums of the merged image weights and of their squares (n_eff, n_eff at equal weights)
     float2 **ring;       // K_max planes [H][W]
     float *sum_pow;      // [H][W]
     float *sum_amp;      // [H][W]
@@ -104,6 +106,14 @@ double inc_beta_cf(double a, double b, double x) {
 
 namespace plk {
 
+std::atomic<long long> g_device_allocations{0};
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_device_allocations.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
 void set_noctx_error(const char *msg) {
     strncpy(g_noctx_err, msg, sizeof(g_noctx_err) - 1);
     g_noctx_err[sizeof(g_noctx_err) - 1] = 0;
@@ -127,21 +137,16 @@ int device_sm_count() {
 using plk::Geom;
 using plk::Planes;
 
-plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
-                                  int *cov_precision, int *ref_scheme, float *ps_da_max) {
-    out->work = ctx->work;
-    plk_params p;
-    if (params) p = *params;
-    else plk_default_params(&p);
-    if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.mu >= 0 && p.mu < 1e6) ||
-        !(p.tol > 0) || p.max_iter < 1 || p.max_iter > 100000 || !(p.cond_max > 0) || !(p.err_max > 0) ||
-        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16 && p.cov_precision != PLK_COV_FP16) ||
-        (p.ref_scheme != PLK_REF_FIRST && p.ref_scheme != PLK_REF_LAST_REAL) ||
-        !(p.ps_da_max >= 0.f && p.ps_da_max < 1e30f))
-        return fail(ctx, PLK_EINVAL, "bad plk_params");
-    if (cov_precision) *cov_precision = p.cov_precision;
-    if (ps_da_max) *ps_da_max = p.ps_da_max;
-    if (ref_scheme) *ref_scheme = p.ref_scheme;
+bool plkapi::params_ok(const plk_params &p) {
+    return (p.alpha > 0 && p.alpha < 1) && (p.beta >= 0 && p.beta < 1) && (p.mu >= 0 && p.mu < 1e6) &&
+           (p.tol > 0) && p.max_iter >= 1 && p.max_iter <= 100000 && (p.cond_max > 0) && (p.err_max > 0) &&
+           (p.cov_precision == PLK_COV_FP32 || p.cov_precision == PLK_COV_BF16 || p.cov_precision == PLK_COV_FP16) &&
+           (p.ref_scheme == PLK_REF_FIRST || p.ref_scheme == PLK_REF_LAST_REAL) &&
+           (p.ps_da_max >= 0.f && p.ps_da_max < 1e30f) && (p.decay > 0.f && p.decay <= 1.f);
+}
+
+void plkapi::emi_params(const plk_params &p, unsigned long long *work, plk::EmiParams *out) {
+    out->work = work;
     out->beta = p.beta;
     out->mu = p.mu;
     out->tol = p.tol;
@@ -149,6 +154,19 @@ plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::E
     out->err_max = p.err_max;
     out->max_iter = p.max_iter;
     out->fp64_resolve = p.fp64_resolve ? 1 : 0;
+}
+
+plk_status plkapi::resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
+                                  int *cov_precision, int *ref_scheme, float *ps_da_max, float *decay) {
+    plk_params p;
+    if (params) p = *params;
+    else plk_default_params(&p);
+    if (!params_ok(p)) return fail(ctx, PLK_EINVAL, "bad plk_params");
+    if (cov_precision) *cov_precision = p.cov_precision;
+    if (ps_da_max) *ps_da_max = p.ps_da_max;
+    if (ref_scheme) *ref_scheme = p.ref_scheme;
+    if (decay) *decay = p.decay;
+    emi_params(p, ctx->work, out);
     if (alpha) *alpha = p.alpha;
     return PLK_OK;
 }
@@ -166,6 +184,7 @@ plk_status plk_default_params(plk_params *p) {
     p->cond_max = 1e4f;
     p->fp64_resolve = 1;
     p->err_max = 0.1f;
+    p->decay = 1.0f;
     return PLK_OK;
 }
 
@@ -181,8 +200,14 @@ int plk_mask_words(plk_window win) { return (win.wy * win.wx + 63) / 64; }
 plk_status plk_glrt_threshold(double alpha, int n_eff, double *c) {
     if (!c || !(alpha > 0.0 && alpha < 1.0) || n_eff < 1)
         return fail(nullptr, PLK_EINVAL, "plk_glrt_threshold: need 0 < alpha < 1, n_eff >= 1");
-    // X = P_p / (P_p + P_q) ~ Beta(n, n); find x with I_x(n, n) = alpha / 2.
-    const double a = n_eff, target = 0.5 * alpha;
+    return plk_glrt_threshold_looks(alpha, (double)n_eff, c);
+}
+
+plk_status plk_glrt_threshold_looks(double alpha, double nu, double *c) {
+    if (!c || !(alpha > 0.0 && alpha < 1.0) || !(nu >= 1.0 && nu < 1e9))
+        return fail(nullptr, PLK_EINVAL, "plk_glrt_threshold_looks: need 0 < alpha < 1, nu >= 1");
+    // X = P_p / (P_p + P_q) ~ Beta(nu, nu); find x with I_x(nu, nu) = alpha / 2.
+    const double a = nu, target = 0.5 * alpha;
     double lo = 0.0, hi = 0.5;
     for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
         const double mid = 0.5 * (lo + hi);
@@ -212,7 +237,7 @@ plk_status plk_create(plk_ctx **out, int device, void *cuda_stream) {
     ctx->work = nullptr;
     {
         DeviceGuard dg(device);
-        if (cudaMalloc(&ctx->work, sizeof(unsigned long long)) != cudaSuccess) {
+        if (plk::dev_malloc((void **)&ctx->work, sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             delete ctx;
             return fail(nullptr, PLK_ENOMEM, "plk_create: device allocation failed");
@@ -695,15 +720,15 @@ plk_status plk_state_create(plk_ctx *ctx, int H, int W, plk_window win, int K_ma
     bool ok = true;
     st->ring = (float2 **)calloc(K_max > 0 ? K_max : 1, sizeof(float2 *));
     ok = ok && st->ring;
-    for (int i = 0; ok && i < K_max; ++i) ok = cudaMalloc(&st->ring[i], npix * sizeof(float2)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->sum_pow, npix * sizeof(float)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->sum_amp, npix * sizeof(float)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->da, npix * sizeof(float)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->amp_new, npix * sizeof(float)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->mask, (nout > 0 ? nout : 1) * g.nwords * sizeof(uint64_t)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->count, (nout > 0 ? nout : 1) * sizeof(uint16_t)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->C, (nout > 0 ? nout : 1) * plk::ntri(Nmax) * sizeof(float2)) == cudaSuccess;
-    ok = ok && cudaMalloc(&st->phase_all, (nout > 0 ? nout : 1) * Nmax * sizeof(float)) == cudaSuccess;
+    for (int i = 0; ok && i < K_max; ++i) ok = plk::dev_malloc((void **)&st->ring[i], npix * sizeof(float2)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->sum_pow, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->sum_amp, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->da, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->amp_new, npix * sizeof(float)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->mask, (nout > 0 ? nout : 1) * g.nwords * sizeof(uint64_t)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->count, (nout > 0 ? nout : 1) * sizeof(uint16_t)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->C, (nout > 0 ? nout : 1) * plk::ntri(Nmax) * sizeof(float2)) == cudaSuccess;
+    ok = ok && plk::dev_malloc((void **)&st->phase_all, (nout > 0 ? nout : 1) * Nmax * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMemsetAsync(st->sum_pow, 0, npix * sizeof(float), ctx->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(st->sum_amp, 0, npix * sizeof(float), ctx->stream) == cudaSuccess;
     if (!ok) {
@@ -728,6 +753,7 @@ plk_status plk_state_reset(plk_state *st) {
     st->n_eff = 0;
     st->steps = 0;
     st->head = 0;
+    st->W1 = st->W2 = 0.0;
     return PLK_OK;
 }
 
@@ -736,6 +762,13 @@ plk_status plk_state_info(const plk_state *st, int *K_used, int *n_eff, int *ste
     if (K_used) *K_used = st->K_used;
     if (n_eff) *n_eff = st->n_eff;
     if (steps) *steps = st->steps;
+    return PLK_OK;
+}
+
+plk_status plk_state_weights(const plk_state *st, double *W1, double *W2) {
+    if (!st) return fail(nullptr, PLK_EINVAL, "plk_state_weights: null state");
+    if (W1) *W1 = st->W1;
+    if (W2) *W2 = st->W2;
     return PLK_OK;
 }
 
@@ -752,7 +785,10 @@ plk_status plk_state_sums(const plk_state *st, const float **sum_pow, const floa
     return PLK_OK;
 }
 
-static const char kMagic[8] = {'P', 'L', 'K', 'S', 'T', 'A', 'T', '1'};
+// Format 2 adds the weight sums W1, W2 (two doubles) after the header;
+// format 1 files (equal weights) load with W1 = W2 = n_eff.
+static const char kMagic[8] = {'P', 'L', 'K', 'S', 'T', 'A', 'T', '2'};
+static const char kMagic1[8] = {'P', 'L', 'K', 'S', 'T', 'A', 'T', '1'};
 
 plk_status plk_state_save(plk_ctx *ctx, const plk_state *st, const char *path) {
     if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_state_save: null ctx");
@@ -765,7 +801,9 @@ plk_status plk_state_save(plk_ctx *ctx, const plk_state *st, const char *path) {
     const long long npix = (long long)st->H * st->W;
     int32_t hdr[10] = {st->H, st->W, st->win.wy, st->win.wx, st->win.sy, st->win.sx,
                        st->K_max, st->K_used, st->n_eff, st->steps};
-    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1;
+    const double wsum[2] = {st->W1, st->W2};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(wsum, sizeof(wsum), 1, f) == 1;
     void *host = malloc(npix * sizeof(float2));
     ok = ok && host;
     for (int i = 0; ok && i < st->K_used; ++i) {
@@ -791,10 +829,19 @@ plk_status plk_state_load(plk_ctx *ctx, const char *path, int M_max, plk_state *
     if (!f) return fail(ctx, PLK_EINVAL, "plk_state_load: cannot open %s", path);
     char magic[8];
     int32_t hdr[10];
-    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, sizeof(hdr), 1, f) != 1) {
+    double wsum[2] = {0.0, 0.0};
+    bool v2 = false;
+    bool hdr_ok = fread(magic, 1, 8, f) == 8;
+    if (hdr_ok) {
+        v2 = memcmp(magic, kMagic, 8) == 0;
+        hdr_ok = (v2 || memcmp(magic, kMagic1, 8) == 0) && fread(hdr, sizeof(hdr), 1, f) == 1;
+    }
+    if (hdr_ok && v2) hdr_ok = fread(wsum, sizeof(wsum), 1, f) == 1;
+    if (!hdr_ok) {
         fclose(f);
         return fail(ctx, PLK_EINVAL, "plk_state_load: not a state file: %s", path);
     }
+    if (!v2) wsum[0] = wsum[1] = hdr[8];
     plk_window win{hdr[2], hdr[3], hdr[4], hdr[5]};
     plk_state *st = nullptr;
     plk_status s = plk_state_create(ctx, hdr[0], hdr[1], win, hdr[6], M_max, &st);
@@ -827,6 +874,8 @@ plk_status plk_state_load(plk_ctx *ctx, const char *path, int M_max, plk_state *
     st->K_used = hdr[7];
     st->n_eff = hdr[8];
     st->steps = hdr[9];
+    st->W1 = wsum[0];
+    st->W2 = wsum[1];
     st->head = 0;
     *out = st;
     return PLK_OK;
@@ -846,9 +895,11 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     plk::EmiParams prm;
     double alpha;
     int cov_precision = PLK_COV_FP32, ref_scheme = PLK_REF_FIRST;
-    float ps_da_max = 0.f;
-    plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision, &ref_scheme, &ps_da_max);
+    float ps_da_max = 0.f, decay = 1.f;
+    plk_status ps = resolve_params(ctx, params, &prm, &alpha, &cov_precision, &ref_scheme, &ps_da_max, &decay);
     if (ps != PLK_OK) return ps;
+    if (decay != 1.f && ps_da_max > 0.f)
+        return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: decaying weights with PS selection");
     if (cov_precision != PLK_COV_FP32 && st->K_used + M > 32)
         return fail(ctx, PLK_EUNSUPPORTED, "plk_ministack_step: tensor-core coherence modes need N <= 32");
     DeviceGuard dg(ctx->device);
@@ -869,14 +920,35 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
     pst.amp_new = st->amp_new;
     pst.n_eff = (float)n_eff;
     pst.da_max = ps_da_max;
+    // Exponentially decaying weights (Sec. III-A): w_j = decay^(M-1-j) for the
+    // new images, decay^M on the running sums, each a product of decays in
+    // double precision rounded once to single precision; W1, W2 carried in
+    // double precision.  decay = 1 takes the equal-weight path unchanged.
+    double W1 = n_eff, W2 = n_eff;
+    plk::SumWeights sw;
+    if (decay != 1.f) {
+        double acc = 1.0, w1 = 0.0, w2 = 0.0;
+        for (int j = M - 1; j >= 0; --j) {
+            sw.w[j] = (float)acc;
+            w1 += (double)sw.w[j];
+            w2 += (double)sw.w[j] * (double)sw.w[j];
+            acc *= (double)decay;
+        }
+        sw.s = (float)acc;
+        W1 = st->n_eff > 0 ? (double)sw.s * st->W1 + w1 : w1;
+        W2 = st->n_eff > 0 ? (double)sw.s * (double)sw.s * st->W2 + w2 : w2;
+    }
     cudaError_t e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(new_slc), M, npix, st->sum_pow,
-                                          st->sum_amp, st->n_eff > 0 ? 1 : 0, s, ps_da_max > 0.f ? &pst : nullptr);
+                                          st->sum_amp, st->n_eff > 0 ? 1 : 0, s, ps_da_max > 0.f ? &pst : nullptr,
+                                          decay != 1.f ? &sw : nullptr);
     ctx->prof.end(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step: amp_stats");
 
-    // S2: SHP masks on the merged statistics.
+    // S2: SHP masks on the merged statistics (nu = W1^2 / W2 looks; n_eff at
+    // equal weights).
     double c;
-    plk_glrt_threshold(alpha, n_eff, &c);
+    if (decay != 1.f) plk_glrt_threshold_looks(alpha, W1 * W1 / W2 < 1.0 ? 1.0 : W1 * W1 / W2, &c);
+    else plk_glrt_threshold(alpha, n_eff, &c);
     uint16_t *cnt = shp_count ? shp_count : st->count;
     ctx->prof.begin("shp_select", s);
     e = plk::launch_shp(st->sum_pow, g, (float)c, st->mask, cnt, s);
@@ -935,9 +1007,53 @@ plk_status plk_ministack_step(plk_ctx *ctx, plk_state *st, const plk_c64 *new_sl
         else st->head = (st->head + 1) % st->K_max;
     }
     st->n_eff = n_eff;
+    st->W1 = W1;
+    st->W2 = W2;
     st->steps += 1;
     return PLK_OK;
 }
+
+plk_status plk_state_enable_host_io(plk_ctx *ctx, plk_state *st) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_state_enable_host_io: null ctx");
+    if (!st) return fail(ctx, PLK_EINVAL, "plk_state_enable_host_io: null state");
+    if (st->device != ctx->device) return fail(ctx, PLK_EINVAL, "plk_state_enable_host_io: state on another device");
+    auto &io = st->io;
+    if (io.ready) return PLK_OK;
+    DeviceGuard dg(ctx->device);
+    const long long npix = (long long)st->H * st->W;
+    const long long nout = (long long)(st->H / st->win.sy) * (st->W / st->win.sx);
+    memset(&io, 0, sizeof(io));
+    const size_t nb = (size_t)st->M_max * npix * sizeof(float2), no = (size_t)(nout > 0 ? nout : 1);
+    bool ok = plk::dev_malloc((void **)&io.stage[0], nb) == cudaSuccess &&
+              plk::dev_malloc((void **)&io.stage[1], nb) == cudaSuccess &&
+              plk::dev_malloc((void **)&io.phase, no * st->M_max * sizeof(float)) == cudaSuccess &&
+              plk::dev_malloc((void **)&io.tcoh, no * sizeof(float)) == cudaSuccess &&
+              plk::dev_malloc((void **)&io.status, no) == cudaSuccess &&
+              plk::dev_malloc((void **)&io.count, no * sizeof(uint16_t)) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&io.copy, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; ok && b < 2; ++b)
+        ok = cudaEventCreateWithFlags(&io.copied[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&io.released[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(io.stage[b]);
+            if (io.copied[b]) cudaEventDestroy(io.copied[b]);
+            if (io.released[b]) cudaEventDestroy(io.released[b]);
+        }
+        cudaFree(io.phase);
+        cudaFree(io.tcoh);
+        cudaFree(io.status);
+        cudaFree(io.count);
+        if (io.copy) cudaStreamDestroy(io.copy);
+        memset(&io, 0, sizeof(io));
+        cudaGetLastError();
+        return fail(ctx, PLK_ENOMEM, "plk_state_enable_host_io: cannot allocate %zu bytes of staging", 2 * nb);
+    }
+    io.ready = true;
+    return PLK_OK;
+}
+
+int64_t plk_device_allocations(void) { return plk::g_device_allocations.load(std::memory_order_relaxed); }
 
 plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
                                    const plk_params *params, float *phase, float *tcoh, uint8_t *status,
@@ -951,34 +1067,8 @@ plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *n
     if (nout > 0 && (!phase || !tcoh || !status)) return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: null output");
     DeviceGuard dg(ctx->device);
     auto &io = st->io;
-    if (!io.ready) {
-        memset(&io, 0, sizeof(io));
-        const size_t nb = (size_t)st->M_max * npix * sizeof(float2), no = (size_t)(nout > 0 ? nout : 1);
-        bool ok = cudaMalloc(&io.stage[0], nb) == cudaSuccess && cudaMalloc(&io.stage[1], nb) == cudaSuccess &&
-                  cudaMalloc(&io.phase, no * st->M_max * sizeof(float)) == cudaSuccess &&
-                  cudaMalloc(&io.tcoh, no * sizeof(float)) == cudaSuccess &&
-                  cudaMalloc(&io.status, no) == cudaSuccess && cudaMalloc(&io.count, no * sizeof(uint16_t)) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&io.copy, cudaStreamNonBlocking) == cudaSuccess;
-        for (int b = 0; ok && b < 2; ++b)
-            ok = cudaEventCreateWithFlags(&io.copied[b], cudaEventDisableTiming) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&io.released[b], cudaEventDisableTiming) == cudaSuccess;
-        if (!ok) {
-            for (int b = 0; b < 2; ++b) {
-                cudaFree(io.stage[b]);
-                if (io.copied[b]) cudaEventDestroy(io.copied[b]);
-                if (io.released[b]) cudaEventDestroy(io.released[b]);
-            }
-            cudaFree(io.phase);
-            cudaFree(io.tcoh);
-            cudaFree(io.status);
-            cudaFree(io.count);
-            if (io.copy) cudaStreamDestroy(io.copy);
-            memset(&io, 0, sizeof(io));
-            cudaGetLastError();
-            return fail(ctx, PLK_ENOMEM, "plk_ministack_step_host: cannot allocate %zu bytes of staging", 2 * nb);
-        }
-        io.ready = true;
-    }
+    if (!io.ready)
+        return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: no staging; call plk_state_enable_host_io first");
     const int b = io.next;
     io.next ^= 1;
     // Copy stream: wait until the step that last read stage[b] has run, then copy.

@@ -29,9 +29,14 @@ plk_status fail(plk_ctx *ctx, plk_status st, const char *fmt, ...);
 plk_status cuda_fail(plk_ctx *ctx, cudaError_t e, const char *what);
 bool window_ok(plk_window w);
 inline bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+// The checks every entry point applies to plk_params, and the kernel
+// parameters they resolve to (work: the device counter of the re-solve).
+bool params_ok(const plk_params &p);
+void emi_params(const plk_params &p, unsigned long long *work, plk::EmiParams *out);
 // plk_params (NULL = defaults) -> kernel parameters, GLRT size and coherence precision.
 plk_status resolve_params(plk_ctx *ctx, const plk_params *params, plk::EmiParams *out, double *alpha,
-                          int *cov_precision = nullptr, int *ref_scheme = nullptr, float *ps_da_max = nullptr);
+                          int *cov_precision = nullptr, int *ref_scheme = nullptr, float *ps_da_max = nullptr,
+                          float *decay = nullptr);
 
 // Make a device current for the duration of a call.
 struct DeviceGuard {

@@ -134,7 +134,7 @@ plk_status plk_batch_create(plk_ctx *ctx, const plk_stack_desc *stacks, int n_st
         total += align256(k.npix * sizeof(float)) + align256(k.nout * nwords * sizeof(uint64_t)) +
                  align256(k.nout * sizeof(uint16_t)) + align256(k.nout * plk::ntri(k.d.N) * sizeof(float2)) + 256;
     }
-    cudaError_t e = cudaMalloc(&b->scratch, total);
+    cudaError_t e = plk::dev_malloc((void **)&b->scratch, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         release(b);

@@ -350,12 +350,18 @@ __device__ __forceinline__ cpx<T> apply_A(const T (&g)[NP], const Loader &load, 
 // ||G||_inf (lambda_min(G^-1 o C) >= lambda_min(G^-1) min_i C_ii = 1 / lambda_max(G)
 // by Schur's bound for a Hadamard product of positive semidefinite matrices);
 // for A = -C it is -1.001 ||C||_inf.  The division is taken only when needed.
+// *used (when given) receives the number of iteration steps taken, rebuilds
+// not counted.  stop_slow (power iteration only): give up as soon as the
+// convergence factor is seen to be slow (q > 0.3 after 4 steps), leaving the
+// rest of the step budget to the caller's refinement.
 template <int NP, class T, class Reform>
 __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cpx<T> &d, T &mu, T &q,
                                                   const Reform &reform, bool allow_reshift, cpx<T> *cbuf, int r,
                                                   bool live, unsigned gmask, T tol, int max_iter,
-                                                  bool build_first, T floor_num = T(0), T floor_den = T(0)) {
+                                                  bool build_first, T floor_num = T(0), T floor_den = T(0),
+                                                  int *used = nullptr, bool stop_slow = false) {
     const T tol2 = tol * tol;
+    if (used) *used = 0;
     d = mk<T>(T(1), T(0));
     q = T(0);
     T dl_prev = T(-1);
@@ -389,6 +395,7 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
             continue;
         }
         if (it - 2 * reshifts >= max_iter) break;
+        if (used) ++*used;
         cpx<T> y = group_matvec<NP, T>(a, x, cbuf, r, gmask);
         if (!live) y = mk<T>(T(0), T(0));
         const T s = group_sum<NP, T>(norm2(y), gmask);          // |y|^2
@@ -404,6 +411,7 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
         if (dl_prev > T(0) && dl > T(100) * tol2) q = sqrt_t(dl / dl_prev);
         dl_prev = dl;
         if (dl <= tol2) return true;
+        if (stop_slow && !allow_reshift && in_round >= 4 && q > T(0.3)) return false;
         if (allow_reshift && reshifts < 3 && in_round >= 4 && q > T(0.3)) {
             // Move the shift towards lambda_min; keep it only if B stays
             // positive definite (the shift is still below lambda_min),
@@ -514,13 +522,19 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     // -lambda_1: rho = x^H C x <= lambda_1 and lambda_1 - lambda_2 ~ (1 - q) rho;
     // a shift that is not below it fails the inertia check and is rebuilt at
     // -1.001 ||C||_inf.  One call site keeps the inlined iteration single.
+    // max_iter caps the steps of both passes together: the power iteration
+    // stops as soon as it is seen to be slow, and the refinement gets what it
+    // left.
     bool conv = false, refined = false, evd_power = inv_failed;
     T fl_num = T(0.999), fl_den = norm_g;
+    int budget = prm.max_iter;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
-        conv = inverse_iteration<NP, T>(a, x, d, mu, q, reform, !evd_power, cbuf, r, live, gmask, tol, prm.max_iter,
-                                        !evd_power, fl_num, fl_den);
-        if (!(evd_power && (!conv || q > T(0.3)))) break;
+        int used = 0;
+        conv = inverse_iteration<NP, T>(a, x, d, mu, q, reform, !evd_power, cbuf, r, live, gmask, tol, budget,
+                                        !evd_power, fl_num, fl_den, &used, evd_power);
+        budget -= used;
+        if (!(evd_power && (!conv || q > T(0.3)) && budget > 0)) break;
         const T rho = d.x;
         T cs = T(0);
 #pragma unroll
@@ -600,7 +614,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
 #else
     if (is_fp64 || inv_failed) out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
 #endif
-    out.status = inv_failed ? PLK_PX_EVD : (!conv ? PLK_PX_NOCONV : (is_fp64 ? PLK_PX_EMI_FP64 : PLK_PX_EMI));
+    out.status = !conv ? PLK_PX_NOCONV : (inv_failed ? PLK_PX_EVD : (is_fp64 ? PLK_PX_EMI_FP64 : PLK_PX_EMI));
     return out;
 }
 

@@ -71,6 +71,31 @@ __global__ void __launch_bounds__(256, 8) k_amp_stats(const float2 *__restrict__
     }
 }
 
+// S1 with exponentially decaying image weights (Sec. III-A): per pixel
+// P_g = sum_j fl(w_j q_j), A_g = sum_j fl(w_j sqrt(q_j)), j ascending, and the
+// running sums become fl(fl(s P) + P_g), fl(fl(s A) + A_g).  Same rounding
+// discipline as k_amp_stats (the sums decide mask bits).
+__global__ void __launch_bounds__(256, 8) k_amp_stats_w(const float2 *__restrict__ z, int n, long long npix,
+                                                      float *__restrict__ sum_pow, float *__restrict__ sum_amp,
+                                                      int accumulate, const SumWeights wts) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
+        float P = 0.0f, A = 0.0f;
+        for (int t = 0; t < n; ++t) {
+            const float2 v = __ldcs(z + (long long)t * npix + p);
+            const float q = __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
+            P = __fadd_rn(P, __fmul_rn(wts.w[t], q));
+            A = __fadd_rn(A, __fmul_rn(wts.w[t], __fsqrt_rn(q)));
+        }
+        if (accumulate) {
+            P = __fadd_rn(__fmul_rn(wts.s, sum_pow[p]), P);
+            if (sum_amp) A = __fadd_rn(__fmul_rn(wts.s, sum_amp[p]), A);
+        }
+        sum_pow[p] = P;
+        if (sum_amp) sum_amp[p] = A;
+    }
+}
+
 // One thread per output pixel; the window's power sums come through L1.
 // Bit b = (dy+hy)*wx + (dx+hx); words are flushed as soon as they fill.
 __global__ void __launch_bounds__(256) k_shp(const float *__restrict__ P, const Geom g, float c,
@@ -130,9 +155,11 @@ static int resident_per_sm(K kernel, int block) {
 }
 
 cudaError_t launch_amp_stats(const float2 *z, int n, long long npix, float *sum_pow, float *sum_amp,
-                             int accumulate, cudaStream_t s, const PsStats *ps) {
+                             int accumulate, cudaStream_t s, const PsStats *ps, const SumWeights *wts) {
     if (npix == 0) return cudaSuccess;
-    if (ps && ps->da && ps->amp_new && sum_amp) {
+    if (wts) {
+        k_amp_stats_w<<<grid_for(npix, 256), 256, 0, s>>>(z, n, npix, sum_pow, sum_amp, accumulate, *wts);
+    } else if (ps && ps->da && ps->amp_new && sum_amp) {
         static int per_sm = 0;  // per process: the kernel's residency does not change
         if (per_sm == 0) per_sm = std::min(8, resident_per_sm(k_amp_stats<true>, 256));
         k_amp_stats<true><<<grid_for(npix, 256, per_sm), 256, 0, s>>>(z, n, npix, sum_pow, sum_amp, accumulate,

@@ -3,20 +3,18 @@
 //
 // Its working buffers (power sums, SHP masks and counts, packed coherence)
 // live in one file-scope __device__ array of PLK_NOALLOC_SCRATCH_BYTES.  Host
-// code cannot use the array's name as a device address, so the first call on
-// each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and keeps it.
+// code cannot use the array's name as a device address: every call looks the
+// address up with cudaGetSymbolAddress, with the calling device current, so
+// the address always belongs to that device's present context (a cached one
+// would be stale after the context is torn down and made again).
 #include <stdio.h>
 #include <string.h>
 
-#include "plk_internal.cuh"
+#include "api_internal.h"
 
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PLK_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Errors are reported through plk_last_error(NULL), like other calls without a context.
 plk_status fail(plk_status st, const char *msg) {
@@ -45,44 +43,55 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
         return fail(PLK_EINVAL, "plk_phase_link_stack_noalloc: misaligned pointer");
 
     // Scratch layout: work counter | sums [H][W] float | mask [Ho][Wo][words] | counts | C.
+    // Every region takes at least a byte per pixel, so sizes past the limit are
+    // refused before any product is formed (no wrap-around in the sum below).
+    const size_t cap = (size_t)PLK_NOALLOC_SCRATCH_BYTES;
     const size_t b_work = 256;
+    size_t need = cap + 1;
+    if ((size_t)npix <= cap && (size_t)nout <= cap) {
+        const size_t b_pow = align256((size_t)npix * sizeof(float));
+        const size_t b_mask = align256((size_t)nout * g.nwords * sizeof(uint64_t));
+        const size_t b_cnt = align256((size_t)nout * sizeof(uint16_t));
+        const size_t b_c = align256((size_t)nout * plk::ntri(N) * sizeof(float2));
+        need = b_work + b_pow + b_mask + b_cnt + b_c;
+    }
+    if (need > cap) {
+        char msg[256];
+        if (need == cap + 1)
+            snprintf(msg, sizeof msg,
+                     "plk_phase_link_stack_noalloc: N=%d, %dx%d needs more scratch than the limit of %zu bytes "
+                     "(PLK_NOALLOC_SCRATCH_BYTES)",
+                     N, H, W, cap);
+        else
+            snprintf(msg, sizeof msg,
+                     "plk_phase_link_stack_noalloc: needs %zu bytes of scratch for N=%d, %dx%d; the limit is %zu "
+                     "(PLK_NOALLOC_SCRATCH_BYTES)",
+                     need, N, H, W, cap);
+        return fail(PLK_EINVAL, msg);
+    }
     const size_t b_pow = align256((size_t)npix * sizeof(float));
     const size_t b_mask = align256((size_t)nout * g.nwords * sizeof(uint64_t));
     const size_t b_cnt = align256((size_t)nout * sizeof(uint16_t));
-    const size_t b_c = align256((size_t)nout * plk::ntri(N) * sizeof(float2));
-    const size_t need = b_work + b_pow + b_mask + b_cnt + b_c;
-    if (need > (size_t)PLK_NOALLOC_SCRATCH_BYTES) {
-        char msg[256];
-        snprintf(msg, sizeof msg,
-                 "plk_phase_link_stack_noalloc: needs %zu bytes of scratch for N=%d, %dx%d; the limit is %zu "
-                 "(PLK_NOALLOC_SCRATCH_BYTES)",
-                 need, N, H, W, (size_t)PLK_NOALLOC_SCRATCH_BYTES);
-        return fail(PLK_EINVAL, msg);
-    }
     plk_params p;
     if (params) p = *params;
     else plk_default_params(&p);
-    if (!(p.alpha > 0 && p.alpha < 1) || !(p.beta >= 0 && p.beta < 1) || !(p.tol > 0) || p.max_iter < 1 ||
-        !(p.cond_max > 0) || !(p.err_max > 0) ||
-        (p.cov_precision != PLK_COV_FP32 && p.cov_precision != PLK_COV_BF16))
-        return fail(PLK_EINVAL, "plk_phase_link_stack_noalloc: bad plk_params");
-    if (p.cov_precision == PLK_COV_BF16 && N > 32)
-        return fail(PLK_EUNSUPPORTED, "plk_phase_link_stack_noalloc: bfloat16 coherence needs N <= 32");
+    if (!plkapi::params_ok(p)) return fail(PLK_EINVAL, "plk_phase_link_stack_noalloc: bad plk_params");
+    if (p.ps_da_max > 0.f)
+        return fail(PLK_EUNSUPPORTED,
+                    "plk_phase_link_stack_noalloc: no persistent-scatterer regridding (ps_da_max must be 0)");
+    if (p.cov_precision != PLK_COV_FP32 && N > 32)
+        return fail(PLK_EUNSUPPORTED, "plk_phase_link_stack_noalloc: tensor-core coherence modes need N <= 32");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(PLK_ECUDA, "plk_phase_link_stack_noalloc: no current CUDA device");
-    if (!g_scratch_addr[dev]) {
-        void *addr = nullptr;
-        e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-        if (e != cudaSuccess || !addr) {
-            cudaGetLastError();
-            return fail(PLK_ECUDA, "plk_phase_link_stack_noalloc: cudaGetSymbolAddress failed");
-        }
-        g_scratch_addr[dev] = addr;
+    if (e != cudaSuccess) return fail(PLK_ECUDA, "plk_phase_link_stack_noalloc: no current CUDA device");
+    void *addr = nullptr;
+    e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess || !addr) {
+        cudaGetLastError();
+        return fail(PLK_ECUDA, "plk_phase_link_stack_noalloc: cudaGetSymbolAddress failed");
     }
-    unsigned char *base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    unsigned char *base = static_cast<unsigned char *>(addr);
     unsigned long long *work = reinterpret_cast<unsigned long long *>(base);
     base += b_work;
     float *sum_pow = reinterpret_cast<float *>(base);
@@ -92,14 +101,7 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
     plk::EmiParams prm;
-    prm.beta = p.beta;
-    prm.mu = p.mu;
-    prm.tol = p.tol;
-    prm.cond_max = p.cond_max;
-    prm.err_max = p.err_max;
-    prm.max_iter = p.max_iter;
-    prm.fp64_resolve = p.fp64_resolve ? 1 : 0;
-    prm.work = work;
+    plkapi::emi_params(p, work, &prm);
 
     // Every scratch region is written in full before it is read in this call.
     e = plk::launch_amp_stats(reinterpret_cast<const float2 *>(slc), N, npix, sum_pow, nullptr, 0, s);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "plk.h"
 
 namespace plk {
@@ -55,8 +57,15 @@ struct PsStats {
     float *da = nullptr, *amp_new = nullptr;
     float n_eff = 0.f, da_max = 0.f;
 };
+// Weights of a decaying merge: image j of the new group weighs w[j], the
+// running sums are scaled by s before the group is added.
+struct SumWeights {
+    float w[PLK_MAX_N] = {};
+    float s = 1.f;
+};
 cudaError_t launch_amp_stats(const float2 *z, int n, long long npix, float *sum_pow, float *sum_amp,
-                             int accumulate, cudaStream_t s, const PsStats *ps = nullptr);
+                             int accumulate, cudaStream_t s, const PsStats *ps = nullptr,
+                             const SumWeights *wts = nullptr);
 cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *mask, uint16_t *count,
                        cudaStream_t s);
 // Returns cudaErrorInvalidConfiguration if the window/N combination exceeds
@@ -79,6 +88,9 @@ cudaError_t launch_covariance_bf16(const Planes &z, int n, const Geom &g, const 
 cudaError_t launch_covariance_fp16(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,
                                    cudaStream_t s);
 struct Prof;
+// cudaMalloc that counts the library's device allocations (plk_device_allocations).
+cudaError_t dev_malloc(void **p, size_t bytes);
+extern std::atomic<long long> g_device_allocations;
 // Where the double-precision re-solve recomputes a pixel's coherence from:
 // the stack planes, geometry and SHP masks of the mini-stack.
 struct StackSource {

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_float), ("mu", ctypes.c_float),
                 ("tol", ctypes.c_float), ("max_iter", ctypes.c_int32), ("cond_max", ctypes.c_float),
                 ("fp64_resolve", ctypes.c_int32), ("err_max", ctypes.c_float), ("cov_precision", ctypes.c_int32),
-                ("ref_scheme", ctypes.c_int32), ("ps_da_max", ctypes.c_float)]
+                ("ref_scheme", ctypes.c_int32), ("ps_da_max", ctypes.c_float), ("decay", ctypes.c_float)]
 
 
 class StackDesc(ctypes.Structure):
@@ -71,6 +71,7 @@ _SIGS = {
     "plk_default_params": [ctypes.POINTER(Params)],
     "plk_output_shape": [_I, _I, Window, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "plk_glrt_threshold": [ctypes.c_double, _I, ctypes.POINTER(ctypes.c_double)],
+    "plk_glrt_threshold_looks": [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     "plk_amp_stats": [_P, _P, _I, _I, _I, _P, _P, _I],
     "plk_shp_select": [_P, _P, _I, _I, _I, Window, ctypes.c_double, _P, _P],
     "plk_estimate_covariance": [_P, _P, _I, _I, _I, Window, _P, _I, _P],
@@ -82,12 +83,14 @@ _SIGS = {
     "plk_state_create": [_P, _I, _I, Window, _I, _I, ctypes.POINTER(_P)],
     "plk_state_destroy": [_P],
     "plk_state_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "plk_state_weights": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "plk_state_kappa": [_P, _I, ctypes.POINTER(_P)],
     "plk_state_sums": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "plk_state_save": [_P, _P, ctypes.c_char_p],
     "plk_state_load": [_P, ctypes.c_char_p, _I, ctypes.POINTER(_P)],
     "plk_ministack_step": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_ministack_step_host": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
+    "plk_state_enable_host_io": [_P, _P],
     "plk_state_reset": [_P],
     "plk_profile_enable": [_P, _I],
     "plk_profile_collect": [_P, ctypes.POINTER(_I)],
@@ -106,7 +109,7 @@ _SIGS = {
     "plk_batch_destroy": [_P],
     "plk_tuned_schedule": [_P, _I, Window, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
 }
-EXPORTS = sorted(list(_SIGS) + ["plk_last_error", "plk_mask_words"])
+EXPORTS = sorted(list(_SIGS) + ["plk_last_error", "plk_mask_words", "plk_device_allocations"])
 
 
 def lib():
@@ -125,6 +128,8 @@ def lib():
             L.plk_last_error.restype = ctypes.c_char_p
             L.plk_mask_words.argtypes = [Window]
             L.plk_mask_words.restype = ctypes.c_int
+            L.plk_device_allocations.argtypes = []
+            L.plk_device_allocations.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -154,6 +159,17 @@ def glrt_threshold(alpha: float, n_eff: int) -> float:
     c = ctypes.c_double()
     _check(lib().plk_glrt_threshold(float(alpha), int(n_eff), ctypes.byref(c)))
     return c.value
+
+
+def glrt_threshold_looks(alpha: float, nu: float) -> float:
+    c = ctypes.c_double()
+    _check(lib().plk_glrt_threshold_looks(float(alpha), float(nu), ctypes.byref(c)))
+    return c.value
+
+
+def device_allocations() -> int:
+    """Device allocations the library has made in this process."""
+    return int(lib().plk_device_allocations())
 
 
 def output_shape(H: int, W: int, win) -> tuple[int, int]:
@@ -530,6 +546,12 @@ class State:
         _check(lib().plk_state_info(self.h, ctypes.byref(k), ctypes.byref(n), ctypes.byref(s)))
         return {"K_used": k.value, "n_eff": n.value, "steps": s.value}
 
+    def weights(self) -> tuple[float, float]:
+        """(W1, W2): sums of the merged image weights and of their squares."""
+        w1, w2 = ctypes.c_double(), ctypes.c_double()
+        _check(lib().plk_state_weights(self.h, ctypes.byref(w1), ctypes.byref(w2)))
+        return w1.value, w2.value
+
     def kappa_ptr(self, i: int) -> int:
         p = ctypes.c_void_p()
         _check(lib().plk_state_kappa(self.h, int(i), ctypes.byref(p)))
@@ -564,12 +586,17 @@ class State:
                self.ctx.h)
         return out
 
+    def enable_host_io(self):
+        """Allocate the device staging of step_host (plk_state_enable_host_io)."""
+        _check(lib().plk_state_enable_host_io(self.ctx.h, self.h), self.ctx.h)
+
     def step_host(self, new_slc: torch.Tensor, params: Params | None = None, out: dict | None = None,
                   want_count: bool = False) -> dict:
         """One step from host memory (plk_ministack_step_host): new_slc a CPU
         complex64 tensor [M, H, W] (pinned, so that its copy overlaps the
-        previous step's compute), outputs written to CPU tensors.  Asynchronous:
-        call ctx.sync() before reading the outputs or reusing new_slc."""
+        previous step's compute), outputs written to CPU tensors.  Needs
+        enable_host_io() first.  Asynchronous: call ctx.sync() before reading
+        the outputs or reusing new_slc."""
         if new_slc.device.type != "cpu" or new_slc.dtype != torch.complex64 or not new_slc.is_contiguous():
             raise TypeError("new_slc: expected a contiguous CPU complex64 tensor")
         M = new_slc.shape[0]

@@ -74,3 +74,28 @@ def test_null_context_is_rejected(libplk):
     assert L.plk_amp_stats(None, None, 1, 1, 1, None, None, 0) == 1
     assert L.plk_phase_link(None, None, 2, 1, 0, None, None, None, None, None) == 1
     assert b"null ctx" in L.plk_last_error(None)
+
+
+def test_glrt_threshold_for_real_looks_matches_oracle(libplk):
+    """plk_glrt_threshold_looks (decaying image weights, nu = W1^2 / W2) against
+    the oracle's F quantile (scipy), and equal to the integer form at integer nu."""
+    import oracle
+    f = libplk.plk_glrt_threshold_looks
+    f.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    for alpha in (1e-3, 0.05):
+        for nu in (1.0, 1.7, 4.25, 9.18, 14.88, 17.45, 29.5):
+            c = ctypes.c_double()
+            assert f(alpha, nu, ctypes.byref(c)) == 0
+            ref = oracle.glrt_threshold_real(alpha, nu)
+            assert abs(c.value - ref) <= 1e-9 * ref, (alpha, nu, c.value, ref)
+            assert np.float32(c.value) == np.float32(ref)
+    c = ctypes.c_double()
+    assert f(1e-3, 0.5, ctypes.byref(c)) == 1 and f(1.5, 3.0, ctypes.byref(c)) == 1   # PLK_EINVAL
+
+
+def test_device_allocation_counter_is_host_only(libplk):
+    f = libplk.plk_device_allocations
+    f.argtypes = []
+    f.restype = ctypes.c_int64
+    assert f() == 0   # nothing allocated in a process that made no context

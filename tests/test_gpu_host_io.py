@@ -45,6 +45,7 @@ def test_host_chain_equals_device_chain(plk, ctx, pinned):
         ref.append({k: v.clone() for k, v in o.items() if v is not None})
     ref_kappa = to_np(dev.kappa(dev.info()["K_used"] - 1)).copy()
     hst = plk.State(ctx, H, W, win, K_max=3, M_max=M)
+    hst.enable_host_io()
     ins = [z[sl].contiguous().pin_memory() if pinned else z[sl].contiguous() for sl in slices]
     outs = [hst.step_host(x, want_count=True) for x in ins]   # no sync in between
     ctx.sync()
@@ -60,10 +61,38 @@ def test_host_chain_equals_device_chain(plk, ctx, pinned):
 
 def test_host_step_rejects_bad_inputs(plk, ctx):
     st = plk.State(ctx, 16, 24, (3, 5, 1, 1), K_max=1, M_max=4)
+    with pytest.raises(plk.PlkError, match="enable_host_io"):
+        st.step_host(torch.zeros((4, 16, 24), dtype=torch.complex64))    # no staging yet
+    st.enable_host_io()
     with pytest.raises(TypeError):
         st.step_host(torch.zeros((4, 16, 24), dtype=torch.complex64, device="cuda"))
     with pytest.raises(ValueError):
         st.step_host(torch.zeros((4, 16, 25), dtype=torch.complex64))
     with pytest.raises(plk.PlkError):
         st.step_host(torch.zeros((5, 16, 24), dtype=torch.complex64))      # M > M_max
+    st.close()
+
+
+def test_steps_allocate_nothing_after_setup(plk, ctx):
+    """Every device allocation happens when the context, the state and the
+    host-I/O staging are made; the steps (device or host buffers, every
+    coherence mode, PS selection, decaying weights) add none."""
+    spec = synth.config_spec(1, N=30, H=60, W=120, seed=31)
+    z = synth.generate(spec)
+    win, M = (5, 11, 3, 6), 10
+    st = plk.State(ctx, 60, 120, win, K_max=2, M_max=M)
+    st.enable_host_io()
+    zg = z.cuda()
+    ctx.sync()
+    before = plk.device_allocations()
+    params = [plk.default_params(), plk.default_params(cov_precision=plk.COV_BF16),
+              plk.default_params(cov_precision=plk.COV_FP16), plk.default_params(ps_da_max=0.2),
+              plk.default_params(decay=0.9)]
+    for p in params:
+        st.reset()
+        for sl in synth.ministack_slices(30, M):
+            st.step(zg[sl].contiguous(), p)
+            st.step_host(z[sl].contiguous(), p)
+        ctx.sync()
+    assert plk.device_allocations() == before
     st.close()

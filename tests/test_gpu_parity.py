@@ -331,3 +331,43 @@ def test_last_real_scheme_noise_free_short_baselines(plk, ctx):
         want = (phi[sl] - phi[ref_date])[:, None, None]
         assert wrapped_diff(to_np(g["phase"]), want).max() < 1e-4, s
     st.close()
+
+
+def _evd_slow_coherences(N, count, seed):
+    """Packed coherences (unit diagonal, positive semidefinite) of three
+    looks whose |C| is indefinite -- the inversion fails and the EVD fallback
+    of Sec. III-B applies -- with lambda_2 / lambda_1 of C above 0.3, so the
+    power iteration is slow and the shifted refinement runs."""
+    rng = np.random.default_rng(seed)
+    iu = np.triu_indices(N)
+    out = []
+    while len(out) < count:
+        Z = rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3))
+        S = Z @ Z.conj().T
+        d = 1.0 / np.sqrt(np.real(np.diag(S)))
+        C = S * np.outer(d, d)
+        if np.linalg.eigvalsh(np.abs(C))[0] > -1e-3:
+            continue
+        w = np.linalg.eigvalsh(C)
+        if w[-2] / w[-1] < 0.35:
+            continue
+        out.append(C[iu])
+    return np.asarray(out).astype(np.complex64)
+
+
+@pytest.mark.parametrize("N", [8, 12])
+def test_evd_fallback_iteration_budget(plk, ctx, N):
+    """max_iter caps the EVD fallback's power iteration and its refinement
+    together: with a budget of 3 steps the slow pixels report NOCONV (last
+    iterate kept, finite phases); with the default budget they converge to the
+    oracle's largest eigenvector of C (status EVD, phase within 1e-4 rad)."""
+    C = _evd_slow_coherences(N, 64, seed=11)
+    o = oracle.phase_link(C.astype(np.complex128), N, 0)
+    assert np.all(o["status"] == plk.PX_EVD)
+    Cg = torch.from_numpy(C).cuda()
+    tight = ctx.phase_link(Cg, N, 0, plk.default_params(max_iter=3, fp64_resolve=0))
+    assert np.all(to_np(tight["status"]) == plk.PX_NOCONV)
+    assert np.all(np.isfinite(to_np(tight["phase"])))
+    full = ctx.phase_link(Cg, N, 0)
+    assert np.all(to_np(full["status"]) == plk.PX_EVD)
+    assert wrapped_diff(to_np(full["phase"]), o["phase"]).max() <= PHASE_TOL

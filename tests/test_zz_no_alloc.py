@@ -27,13 +27,14 @@ def plk():
     return _plk
 
 
-def test_noalloc_matches_allocating_path_twice(plk):
+@pytest.mark.parametrize("cov_precision", ["fp32", "fp16"])
+def test_noalloc_matches_allocating_path_twice(plk, cov_precision):
     from paper_2511_12051_gb300 import synth
     L = plk.lib()
     ctx = plk.Context("cuda:0")
     win = (5, 11, 3, 6)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    params = plk.default_params()
+    params = plk.default_params(cov_precision={"fp32": plk.COV_FP32, "fp16": plk.COV_FP16}[cov_precision])
     for seed in (41, 42):
         spec = synth.config_spec(1, H=96, W=300, seed=seed)
         z = synth.generate(spec).cuda()
@@ -65,3 +66,23 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(plk):
                                         _p(out), _p(out), None, None)
     assert rc == 1
     assert b"PLK_NOALLOC_SCRATCH_BYTES" in L.plk_last_error(None)
+
+
+def test_noalloc_rejects_what_it_does_not_compute(plk):
+    """PS regridding is a plk_ministack_step option this entry point does not
+    run: asked for, it refuses instead of returning plain EMI phases.  Bad
+    parameters are rejected by the same checks as the other entry points."""
+    L = plk.lib()
+    z = torch.zeros((15, 30, 60), dtype=torch.complex64, device="cuda")
+    out = torch.zeros((15, 10, 10), device="cuda")
+    st = torch.zeros((10, 10), dtype=torch.uint8, device="cuda")
+    win = plk.window((5, 11, 3, 6))
+    p = plk.default_params(ps_da_max=0.2)
+    rc = L.plk_phase_link_stack_noalloc(_p(z), 15, 30, 60, win, 0, ctypes.byref(p), _p(out), _p(out), _p(st), None,
+                                        None)
+    assert rc == 5, L.plk_last_error(None)      # PLK_EUNSUPPORTED
+    for bad in ({"mu": -1.0}, {"mu": float("nan")}, {"tol": 0.0}, {"cov_precision": 7}, {"ref_scheme": 9}):
+        p = plk.default_params(**bad)
+        rc = L.plk_phase_link_stack_noalloc(_p(z), 15, 30, 60, win, 0, ctypes.byref(p), _p(out), _p(out), _p(st),
+                                            None, None)
+        assert rc == 1, (bad, L.plk_last_error(None))  # PLK_EINVAL
