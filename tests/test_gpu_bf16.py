@@ -17,11 +17,14 @@ from parity_util import to_np, wrapped_diff
 
 pytestmark = pytest.mark.gpu
 
-# Measured bounds of the bfloat16 mode against the FP64 oracle on the
-# unrounded samples (burst-shaped stacks, 11x5 window, strides 6x3).
-BF16_COH_MAX = 2e-2       # max |C_bf16 - C| over all entries
-BF16_PHASE_P99 = 5e-2     # rad, 99th percentile of the linked-phase error
-BF16_PHASE_P50 = 1e-2     # rad, median
+# Bounds of the bfloat16 mode against the FP64 oracle on the unrounded samples
+# (burst-shaped 90x300 stack, N = 15, 11x5 window, strides 6x3), each at most
+# twice the measured value: coherence max error 3.9e-3; linked phase p50
+# 1.10e-3, p99 3.00e-3, max 7.63e-3 rad.
+BF16_COH_MAX = 7.8e-3     # max |C_bf16 - C| over all entries
+BF16_PHASE_P99 = 6e-3     # rad, 99th percentile of the linked-phase error
+BF16_PHASE_P50 = 2.2e-3   # rad, median
+BF16_PHASE_MAX = 1.5e-2   # rad, largest
 
 
 @pytest.fixture(scope="module")
@@ -113,6 +116,7 @@ def test_bf16_mode_bounds(ctx, plk):
     assert coh_err.max() < BF16_COH_MAX
     assert p50 < BF16_PHASE_P50
     assert p99 < BF16_PHASE_P99
+    assert mx < BF16_PHASE_MAX
 
 
 def test_bf16_ministack_step_runs_and_tracks_fp32(ctx, plk):

@@ -23,11 +23,13 @@ from parity_util import to_np, wrapped_diff
 
 pytestmark = pytest.mark.gpu
 
-# Measured (burst-shaped 90x300 stack, N = 15, 11x5, strides 6x3): coherence
-# max error 4.0e-4; phase p50 1.4e-4, p99 3.7e-4, max 5.9e-4 rad.
-FP16_COH_MAX = 2e-3      # max |C_fp16 - C| over all entries
-FP16_PHASE_P99 = 2e-3    # rad, 99th percentile of the linked-phase error
-FP16_PHASE_P50 = 1e-3    # rad, median
+# Bounds at most twice the measured values (burst-shaped 90x300 stack, N = 15,
+# 11x5, strides 6x3): coherence max error 4.0e-4; phase p50 1.36e-4, p99
+# 3.72e-4, max 5.91e-4 rad.
+FP16_COH_MAX = 8e-4      # max |C_fp16 - C| over all entries
+FP16_PHASE_P99 = 7.4e-4  # rad, 99th percentile of the linked-phase error
+FP16_PHASE_P50 = 2.7e-4  # rad, median
+FP16_PHASE_MAX = 1.18e-3 # rad, largest
 
 
 @pytest.fixture(scope="module")
@@ -127,6 +129,7 @@ def test_fp16_mode_bounds(ctx, plk):
     assert coh_err.max() < FP16_COH_MAX
     assert p50 < FP16_PHASE_P50
     assert p99 < FP16_PHASE_P99
+    assert mx < FP16_PHASE_MAX
 
 
 def test_fp16_ministack_step_tracks_fp32(ctx, plk):
