@@ -371,3 +371,34 @@ def test_evd_fallback_iteration_budget(plk, ctx, N):
     full = ctx.phase_link(Cg, N, 0)
     assert np.all(to_np(full["status"]) == plk.PX_EVD)
     assert wrapped_diff(to_np(full["phase"]), o["phase"]).max() <= PHASE_TOL
+
+
+@pytest.mark.parametrize("win", [(5, 11, 3, 6), (5, 11, 1, 1), (3, 3, 4, 4)])
+def test_step_equals_the_separate_calls(plk, ctx, win):
+    """plk_ministack_step equals the separate C-ABI calls plk_amp_stats,
+    plk_shp_select, plk_estimate_covariance and plk_phase_link on the same
+    stack: sums, masks and counts bit for bit, and the same phases, gamma_t and
+    statuses, over two steps (the second merges into the running sums).  The
+    double-precision re-solve is off on both sides: by design the step
+    recomputes a flagged pixel's coherence from the stack, plk_phase_link from
+    its single-precision input.  The image size leaves rows and columns outside
+    every decimation block."""
+    z, _ = stack(1, N=20, H=97, W=301, seed=13)
+    zg = z.cuda()
+    M = 10
+    H, W = z.shape[1:]
+    p = plk.default_params(fp64_resolve=0)
+    st = plk.State(ctx, H, W, win, K_max=0, M_max=M)
+    sp, sa = None, torch.empty((H, W), device="cuda")
+    same = lambda a, b: torch.equal(torch.nan_to_num(a, nan=-9.0), torch.nan_to_num(b, nan=-9.0))
+    for k, sl in enumerate(synth.ministack_slices(20, M)):
+        g = st.step(zg[sl].contiguous(), p)
+        sp, sa = ctx.amp_stats(zg[sl].contiguous(), sp, sa, accumulate=k > 0)
+        mask, cnt = ctx.shp_select(sp, M * (k + 1), win)
+        C = ctx.estimate_covariance(zg[sl].contiguous(), win, mask)
+        o = ctx.phase_link(C, M, 0, p)
+        assert torch.equal(st.sum_pow(), sp), k
+        assert torch.equal(g["count"], cnt), k
+        assert torch.equal(g["status"], o["status"]), k
+        assert same(g["phase"], o["phase"]) and same(g["tcoh"], o["tcoh"]), k
+    st.close()
