@@ -652,18 +652,26 @@ def main():
         torch.cuda.synchronize(dev)
         link_gbs = bi / (l0.elapsed_time(l1) / 1e3) / 1e9
         pdist.barrier()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        ne = max(1, min(args.steps, 10))
-        f0.record(stream)
-        for _ in range(ne):
+        # An event on the compute stream after each call marks when that step's
+        # outputs are back in host memory: the first interval holds the first
+        # copy and the first step back to back (nothing to overlap yet), the
+        # later ones the steady state, where the copy of step i+1 runs under
+        # the compute of step i.
+        ne = max(2, min(2 * args.steps, 20))
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(ne + 1)]
+        fe[0].record(stream)
+        for i in range(ne):
             e2e_step()
-        f1.record(stream)
+            fe[i + 1].record(stream)
         ctx.sync()
         torch.cuda.synchronize(dev)
-        ms_e2e = pdist.max_over_ranks(f0.elapsed_time(f1), dev)
+        ms_e2e = pdist.max_over_ranks(fe[0].elapsed_time(fe[ne]), dev)
+        iv = [fe[i].elapsed_time(fe[i + 1]) for i in range(ne)]
+        steady = sorted(iv[1:])[len(iv[1:]) // 2] if ne > 1 else iv[0]
         e2e = {"value": npx * world * ne / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_e2e / ne,
+               "first_step_ms": iv[0], "steady_median_ms": steady, "compute_alone_ms": ms_step,
+               "intervals_ms": [round(v, 1) for v in iv],
                "h2d_link_gbs": link_gbs, "input_copy_bound_ms": bi / (link_gbs * 1e9) * 1e3}
         del zh, oh
 

@@ -237,7 +237,7 @@ plk_status plk_create(plk_ctx **out, int device, void *cuda_stream) {
     ctx->work = nullptr;
     {
         DeviceGuard dg(device);
-        if (plk::dev_malloc((void **)&ctx->work, sizeof(unsigned long long)) != cudaSuccess) {
+        if (plk::dev_malloc((void **)&ctx->work, plk::kEmiWorkBytes) != cudaSuccess) {
             cudaGetLastError();
             delete ctx;
             return fail(nullptr, PLK_ENOMEM, "plk_create: device allocation failed");

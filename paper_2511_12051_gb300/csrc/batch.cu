@@ -132,7 +132,7 @@ plk_status plk_batch_create(plk_ctx *ctx, const plk_stack_desc *stacks, int n_st
         k.c = (float)c;
         k.cost = (double)k.nout * ((double)k.d.N * k.d.N * win.wy * win.wx + (double)k.d.N * k.d.N * k.d.N);
         total += align256(k.npix * sizeof(float)) + align256(k.nout * nwords * sizeof(uint64_t)) +
-                 align256(k.nout * sizeof(uint16_t)) + align256(k.nout * plk::ntri(k.d.N) * sizeof(float2)) + 256;
+                 align256(k.nout * sizeof(uint16_t)) + align256(k.nout * plk::ntri(k.d.N) * sizeof(float2)) + align256(plk::kEmiWorkBytes);
     }
     cudaError_t e = plk::dev_malloc((void **)&b->scratch, total);
     if (e != cudaSuccess) {
@@ -151,7 +151,7 @@ plk_status plk_batch_create(plk_ctx *ctx, const plk_stack_desc *stacks, int n_st
         k.C = reinterpret_cast<float2 *>(p);
         p += align256(k.nout * plk::ntri(k.d.N) * sizeof(float2));
         k.work = reinterpret_cast<unsigned long long *>(p);
-        p += 256;
+        p += align256(plk::kEmiWorkBytes);
     }
     // The graph's origin and branch streams (non-blocking: the legacy default
     // stream cannot be recorded from).

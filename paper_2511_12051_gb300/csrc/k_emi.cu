@@ -38,19 +38,74 @@ struct PackedRow {
 
 constexpr int kEmiWarps = 4;
 
-// Work counter of the double-precision re-solve (one per context): warps take
-// 32-pixel chunks of the status array in turn, so the few long-running pending
-// pixels spread over all resident warps instead of waiting for the chunks
-// statically assigned to them.  Chunk c holds pixels c, c + nchunks, ...,
-// c + 31 nchunks: pending pixels cluster in space, and interleaving spreads a
-// cluster over many chunks (and warps).  Reset by k_reset_counter before each re-solve
-// launch (stream order).
-__global__ void k_reset_counter(unsigned long long *c) { *c = 0; }
+// Work area of the double-precision re-solve (kEmiWorkBytes, one per context,
+// batch stack or allocation-free call): the single-precision pass appends each
+// pixel it flags to the pending list, and the re-solve's warps take list
+// entries two groups at a time from a cursor, so the pending pixels spread
+// evenly over every resident group whatever their layout, and no warp walks
+// the status array.  When more pixels are flagged than the list holds, the
+// re-solve falls back to the status scan: warps take 32-pixel chunks of the
+// status array in turn, chunk c holding pixels c, c + nchunks, ..., c + 31
+// nchunks (pending pixels cluster in space, and interleaving spreads a cluster
+// over many chunks and warps).  k_reset_counter zeroes the three counters
+// before the single-precision pass (stream order).
+__global__ void k_reset_counter(unsigned long long *c) {
+    if (threadIdx.x < 3) c[threadIdx.x] = 0;
+}
 
-__device__ __forceinline__ long long next_chunk(unsigned long long *counter, int lane) {
+__device__ __forceinline__ long long next_chunk(unsigned long long *counter, int lane, unsigned long long inc = 1) {
     unsigned long long c = 0;
-    if (lane == 0) c = atomicAdd(counter, 1ull);
+    if (lane == 0) c = atomicAdd(counter, inc);
     return (long long)__shfl_sync(0xffffffffu, c, 0);
+}
+
+// Append pixel p to the pending list (one lane of its group).
+__device__ __forceinline__ void append_pending(unsigned long long *work, long long p) {
+    const unsigned long long i = atomicAdd(work + 1, 1ull);
+    if (i < (unsigned long long)kPendCap) pending_list(work)[i] = (unsigned)p;
+}
+
+// The re-solve's loop over pending pixels: solve(p) for each, one NP-lane
+// group at a time; list mode when the list held every flagged pixel, the
+// status scan otherwise.
+template <int NP, class Solve>
+__device__ __forceinline__ void for_each_pending(unsigned long long *work, bool use_list, long long npx,
+                                                 const uint8_t *status, int lane, const Solve &solve) {
+    constexpr int G = 32 / NP;
+    const int grp = lane / NP;
+    const unsigned long long cnt = use_list ? *(volatile unsigned long long *)(work + 1) : ~0ull;
+    if (cnt <= (unsigned long long)kPendCap) {
+        const unsigned *lst = pending_list(work);
+        for (;;) {
+            const long long b0 = next_chunk(work + 2, lane, (unsigned long long)G);
+            if (b0 >= (long long)cnt) break;
+            const long long i = b0 + grp;
+            if (i < (long long)cnt) solve((long long)lst[i]);
+            __syncwarp();
+        }
+        return;
+    }
+    const long long nchunks = (npx + 31) / 32;
+    for (;;) {
+        const long long base = next_chunk(work, lane);
+        if (base >= nchunks) break;
+        const long long pl = base + (long long)lane * nchunks;  // interleaved: clusters spread over chunks
+        const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
+        unsigned bal = __ballot_sync(0xffffffffu, pend);
+        while (bal) {
+            int mine = -1;
+#pragma unroll
+            for (int gg = 0; gg < G; ++gg) {
+                if (bal) {
+                    const int b = __ffs(bal) - 1;
+                    if (gg == grp) mine = b;
+                    bal &= bal - 1u;
+                }
+            }
+            if (mine >= 0) solve(base + (long long)mine * nchunks);
+            __syncwarp();
+        }
+    }
 }
 // CTAs per SM the single-precision kernel is register-budgeted for (NP <= 16).
 #ifndef PLK_EMI_MINB
@@ -92,7 +147,8 @@ template <int NP>
 __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi32(const float2 *__restrict__ C, int n, long long npx,
                                                           int ref, const EmiParams prm,
                                                           float *__restrict__ phase, float *__restrict__ tcoh,
-                                                          float *__restrict__ lam, uint8_t *__restrict__ status) {
+                                                          float *__restrict__ lam, uint8_t *__restrict__ status,
+                                                          bool use_list) {
     constexpr bool kPow2 = (NP & (NP - 1)) == 0;
     constexpr int G = kPow2 ? 32 / NP : 1;
     constexpr bool kPf = EmiPrefetch<NP>::on;
@@ -173,7 +229,10 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
             SmemRow<NP> ld{myrow};
             const PixelResult res = emi_solve<NP, float>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0, false);
             if (res.flag) {
-                if (r == 0) status[p] = (uint8_t)kPending;
+                if (r == 0) {
+                    status[p] = (uint8_t)kPending;
+                    if (use_list) append_pending(prm.work, p);
+                }
             } else {
                 if (r < n) phase[(long long)r * npx + p] = res.phase;
                 if (r == 0) {
@@ -195,52 +254,30 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
     if constexpr (kPf) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Double-precision re-solve of the pixels left pending.  Each warp scans 32
-// statuses at a time, ballots the pending ones and hands them out, one per
-// NP-lane group, until the chunk is done.
+// Double-precision re-solve of the pixels left pending, one per NP-lane group
+// as for_each_pending hands them out.
 template <int NP>
 __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restrict__ C, int n, long long npx,
                                                           int ref, const EmiParams prm,
                                                           float *__restrict__ phase, float *__restrict__ tcoh,
-                                                          float *__restrict__ lam, uint8_t *__restrict__ status) {
-    constexpr int G = 32 / NP;
+                                                          float *__restrict__ lam, uint8_t *__restrict__ status,
+                                                          bool use_list) {
     __shared__ __align__(16) cpx<double> sbuf[kEmiWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / NP, r = lane - grp * NP;
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
-    const long long nchunks = (npx + 31) / 32;
-    for (;;) {
-        const long long base = next_chunk(prm.work, lane);
-        if (base >= nchunks) break;
-        const long long pl = base + (long long)lane * nchunks;  // interleaved: clusters spread over chunks
-        const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
-        unsigned bal = __ballot_sync(0xffffffffu, pend);
-        while (bal) {
-            int mine = -1;
-#pragma unroll
-            for (int gg = 0; gg < G; ++gg) {
-                if (bal) {
-                    const int b = __ffs(bal) - 1;
-                    if (gg == grp) mine = b;
-                    bal &= bal - 1u;
-                }
-            }
-            if (mine >= 0) {
-                const long long p = base + (long long)mine * nchunks;
-                PackedRow<double> ld{C + p * nt, n, r};
-                const PixelResult res = emi_solve_mixed<NP>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0);
-                if (r < n) phase[(long long)r * npx + p] = res.phase;
-                if (r == 0) {
-                    if (tcoh) tcoh[p] = res.tcoh;
-                    if (lam) lam[p] = res.lam;
-                    status[p] = (uint8_t)res.status;
-                }
-            }
-            __syncwarp();
+    for_each_pending<NP>(prm.work, use_list, npx, status, lane, [&](long long p) {
+        PackedRow<double> ld{C + p * nt, n, r};
+        const PixelResult res = emi_solve_mixed<NP>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0);
+        if (r < n) phase[(long long)r * npx + p] = res.phase;
+        if (r == 0) {
+            if (tcoh) tcoh[p] = res.tcoh;
+            if (lam) lam[p] = res.lam;
+            status[p] = (uint8_t)res.status;
         }
-    }
+    });
 }
 
 // Row source held in registers (indexed with compile-time k after inlining).
@@ -283,98 +320,76 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
                                                                 long long npx, int ref, const EmiParams prm,
                                                                 float *__restrict__ phase, float *__restrict__ tcoh,
                                                                 float *__restrict__ lam,
-                                                                uint8_t *__restrict__ status) {
-    constexpr int G = 32 / NP;
+                                                                uint8_t *__restrict__ status, bool use_list) {
     constexpr int E = 16 / sizeof(cpx<double>);
     __shared__ __align__(16) cpx<double> sbuf[kEmiWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / NP, r = lane - grp * NP;
     const int glane0 = grp * NP;
     const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
-    const long long nchunks = (npx + 31) / 32;
-    for (;;) {
-        const long long base = next_chunk(prm.work, lane);
-        if (base >= nchunks) break;
-        const long long pl = base + (long long)lane * nchunks;  // interleaved: clusters spread over chunks
-        const bool pend = pl < npx && status[pl] == (uint8_t)kPending;
-        unsigned bal = __ballot_sync(0xffffffffu, pend);
-        while (bal) {
-            int mine = -1;
+    for_each_pending<NP>(prm.work, use_list, npx, status, lane, [&](long long p) {
+        const int oy = (int)(p / g.Wo), ox = (int)(p - (p / g.Wo) * g.Wo);
+        const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
+        const uint64_t *mw = mask + p * g.nwords;
+        F2 re[NP], im[NP];
 #pragma unroll
-            for (int gg = 0; gg < G; ++gg) {
-                if (bal) {
-                    const int b = __ffs(bal) - 1;
-                    if (gg == grp) mine = b;
-                    bal &= bal - 1u;
-                }
-            }
-            if (mine >= 0) {
-                const long long p = base + (long long)mine * nchunks;
-                const int oy = (int)(p / g.Wo), ox = (int)(p - (p / g.Wo) * g.Wo);
-                const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
-                const uint64_t *mw = mask + p * g.nwords;
-                F2 re[NP], im[NP];
+        for (int k = 0; k < NP; ++k) re[k] = im[k] = F2{0.f, 0.f};
+        int b = 0;
+        uint64_t word = __ldg(mw);
+        for (int dy = -g.hy; dy <= g.hy; ++dy)
+            for (int dx = -g.hx; dx <= g.hx; ++dx, ++b) {
+                if ((b & 63) == 0 && b > 0) word = __ldg(mw + (b >> 6));
+                if (!((word >> (b & 63)) & 1ull)) continue;
+                const long long q = (long long)(cy + dy) * g.W + (cx + dx);
+                float2 zr = make_float2(0.f, 0.f);
+                if (r < n) zr = __ldg(z.p[r] + q);
 #pragma unroll
-                for (int k = 0; k < NP; ++k) re[k] = im[k] = F2{0.f, 0.f};
-                int b = 0;
-                uint64_t word = __ldg(mw);
-                for (int dy = -g.hy; dy <= g.hy; ++dy)
-                    for (int dx = -g.hx; dx <= g.hx; ++dx, ++b) {
-                        if ((b & 63) == 0 && b > 0) word = __ldg(mw + (b >> 6));
-                        if (!((word >> (b & 63)) & 1ull)) continue;
-                        const long long q = (long long)(cy + dy) * g.W + (cx + dx);
-                        float2 zr = make_float2(0.f, 0.f);
-                        if (r < n) zr = __ldg(z.p[r] + q);
-#pragma unroll
-                        for (int k = 0; k < NP; ++k) {
-                            if (k < n) {
-                                const float2 zk = __ldg(z.p[k] + q);
-                                // z_r conj(z_k) = (xr xk + yr yk) + j (yr xk - xr yk)
-                                f2_add_prod(re[k], zr.x, zk.x);
-                                f2_add_prod(re[k], zr.y, zk.y);
-                                f2_add_prod(im[k], zr.y, zk.x);
-                                f2_add_prod(im[k], -zr.x, zk.y);
-                            }
-                        }
-                    }
-                RegRow<NP, double> row;
-#pragma unroll
-                for (int k = 0; k < NP; ++k) row.c[k] = mk<double>(f2_value(re[k]), f2_value(im[k]));
-                // normalise: C_rk = S_rk s_r s_k with s_i = 1/sqrt(S_ii) (0 when
-                // S_ii = 0), C_rr = 1; one square root per lane.
-                cpx<double> *buf = &sbuf[warp][glane0];
-                double d_own = 0.0;
-#pragma unroll
-                for (int k = 0; k < NP; ++k)
-                    if (k == r) d_own = row.c[k].x;
-                const double s_own = (d_own > 0.0) ? 1.0 / sqrt(d_own) : 0.0;
-                buf[r] = mk<double>(s_own, 0.0);
-                __syncwarp(gmask);
-                const uint4 *src = reinterpret_cast<const uint4 *>(buf);
-#pragma unroll
-                for (int q4 = 0; q4 < NP / E; ++q4) {
-                    const uint4 v = src[q4];
-                    cpx<double> sk[E];
-                    memcpy(sk, &v, 16);
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const int k = q4 * E + e;
-                        const double sc = s_own * sk[e].x;
-                        row.c[k] = (k == r) ? mk<double>(1.0, 0.0) : mk<double>(row.c[k].x * sc, row.c[k].y * sc);
+                for (int k = 0; k < NP; ++k) {
+                    if (k < n) {
+                        const float2 zk = __ldg(z.p[k] + q);
+                        // z_r conj(z_k) = (xr xk + yr yk) + j (yr xk - xr yk)
+                        f2_add_prod(re[k], zr.x, zk.x);
+                        f2_add_prod(re[k], zr.y, zk.y);
+                        f2_add_prod(im[k], zr.y, zk.x);
+                        f2_add_prod(im[k], -zr.x, zk.y);
                     }
                 }
-                __syncwarp(gmask);
-                const PixelResult res = emi_solve_mixed<NP>(row, r, n, ref, prm, buf, gmask, glane0);
-                if (r < n) phase[(long long)r * npx + p] = res.phase;
-                if (r == 0) {
-                    if (tcoh) tcoh[p] = res.tcoh;
-                    if (lam) lam[p] = res.lam;
-                    status[p] = (uint8_t)res.status;
-                }
             }
-            __syncwarp();
+        RegRow<NP, double> row;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) row.c[k] = mk<double>(f2_value(re[k]), f2_value(im[k]));
+        // normalise: C_rk = S_rk s_r s_k with s_i = 1/sqrt(S_ii) (0 when
+        // S_ii = 0), C_rr = 1; one square root per lane.
+        cpx<double> *buf = &sbuf[warp][glane0];
+        double d_own = 0.0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+            if (k == r) d_own = row.c[k].x;
+        const double s_own = (d_own > 0.0) ? 1.0 / sqrt(d_own) : 0.0;
+        buf[r] = mk<double>(s_own, 0.0);
+        __syncwarp(gmask);
+        const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+#pragma unroll
+        for (int q4 = 0; q4 < NP / E; ++q4) {
+            const uint4 v = src[q4];
+            cpx<double> sk[E];
+            memcpy(sk, &v, 16);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = q4 * E + e;
+                const double sc = s_own * sk[e].x;
+                row.c[k] = (k == r) ? mk<double>(1.0, 0.0) : mk<double>(row.c[k].x * sc, row.c[k].y * sc);
+            }
         }
-    }
+        __syncwarp(gmask);
+        const PixelResult res = emi_solve_mixed<NP>(row, r, n, ref, prm, buf, gmask, glane0);
+        if (r < n) phase[(long long)r * npx + p] = res.phase;
+        if (r == 0) {
+            if (tcoh) tcoh[p] = res.tcoh;
+            if (lam) lam[p] = res.lam;
+            status[p] = (uint8_t)res.status;
+        }
+    });
 }
 
 template <int NP>
@@ -386,8 +401,12 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
     const long long cap = (long long)device_sm_count() * 16;
     long long blocks = ((npx + G - 1) / G + kEmiWarps - 1) / kEmiWarps;
     blocks = blocks > cap ? cap : (blocks < 1 ? 1 : blocks);
+    // pixel indices of the pending list are 32-bit
+    const bool use_list = npx <= 0xffffffffLL;
+    if (prm.fp64_resolve) k_reset_counter<<<1, 32, 0, s>>>(prm.work);
     if (prof) prof->begin("phase_link_fp32", s);
-    k_emi32<NP><<<(unsigned)blocks, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status);
+    k_emi32<NP><<<(unsigned)blocks, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status,
+                                                           use_list && prm.fp64_resolve);
     cudaError_t e = cudaGetLastError();
     if (prof) prof->end(s);
     if (e != cudaSuccess || !prm.fp64_resolve) return e;
@@ -395,12 +414,12 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
     const long long cap64 = (long long)device_sm_count() * 2;  // resident CTAs at this kernel's register use
     blocks64 = blocks64 > cap64 ? cap64 : (blocks64 < 1 ? 1 : blocks64);
     if (prof) prof->begin("phase_link_fp64", s);
-    k_reset_counter<<<1, 1, 0, s>>>(prm.work);
     if (src)
         k_emi64_stack<NP64><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(*src->z, *src->g, src->mask, n, npx, ref,
-                                                                          prm, phase, tcoh, lam, status);
+                                                                          prm, phase, tcoh, lam, status, use_list);
     else
-        k_emi64<NP64><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status);
+        k_emi64<NP64><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status,
+                                                                    use_list);
     e = cudaGetLastError();
     if (prof) prof->end(s);
     return e;

@@ -42,11 +42,11 @@ extern "C" plk_status plk_phase_link_stack_noalloc(const plk_c64 *slc, int N, in
         (shp_count && ((uintptr_t)shp_count % 2)))
         return fail(PLK_EINVAL, "plk_phase_link_stack_noalloc: misaligned pointer");
 
-    // Scratch layout: work counter | sums [H][W] float | mask [Ho][Wo][words] | counts | C.
+    // Scratch layout: re-solve work area | sums [H][W] float | mask [Ho][Wo][words] | counts | C.
     // Every region takes at least a byte per pixel, so sizes past the limit are
     // refused before any product is formed (no wrap-around in the sum below).
     const size_t cap = (size_t)PLK_NOALLOC_SCRATCH_BYTES;
-    const size_t b_work = 256;
+    const size_t b_work = align256(plk::kEmiWorkBytes);
     size_t need = cap + 1;
     if ((size_t)npix <= cap && (size_t)nout <= cap) {
         const size_t b_pow = align256((size_t)npix * sizeof(float));

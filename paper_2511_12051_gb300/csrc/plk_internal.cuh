@@ -40,8 +40,19 @@ struct EmiParams {
     float beta, mu, tol, cond_max, err_max;
     int max_iter;
     int fp64_resolve;
-    unsigned long long *work;  // device work counter of the FP64 re-solve (owned by the caller's context)
+    unsigned long long *work;  // device work area of the FP64 re-solve, kEmiWorkBytes (owned by the caller)
 };
+
+// Work area of one phase-link launch pair: counter 0 is the re-solve's chunk
+// cursor over the status array, counter 1 the length of the pending list the
+// single-precision pass appends to, counter 2 the re-solve's cursor in that
+// list; the list (kPendCap pixel indices) starts at byte 256.  A longer
+// pending set overflows the list and the re-solve scans the statuses instead.
+constexpr int kPendCap = 65536;
+constexpr size_t kEmiWorkBytes = 256 + (size_t)kPendCap * sizeof(unsigned);
+__host__ __device__ inline unsigned *pending_list(unsigned long long *work) {
+    return reinterpret_cast<unsigned *>(reinterpret_cast<char *>(work) + 256);
+}
 
 __host__ __device__ inline long long ntri(int n) { return (long long)n * (n + 1) / 2; }
 __host__ __device__ inline int packed_index(int n, int i, int k) { return i * n - i * (i - 1) / 2 + (k - i); }

@@ -4,6 +4,10 @@ import torch
 
 PHASE_TOL = 1e-4   # rad, single precision vs the FP64 oracle
 TCOH_TOL = 1e-5
+# Relative eigengap (lambda_2 - lambda_1) / |lambda_1| below which the
+# eigenvector is not unique (several answers are correct): such pixels are left
+# out of phase parity and counted; gamma_t is still compared.
+GAP_MIN = 1e-9
 
 
 def wrapped_diff(a, b):
@@ -50,3 +54,11 @@ def write_state_file(path, chain, M_max=None):
             f.write(np.ascontiguousarray(k, np.complex64).tobytes())
         f.write(np.ascontiguousarray(chain.sum_pow, np.float32).tobytes())
         f.write(np.ascontiguousarray(chain.sum_amp, np.float32).tobytes())
+
+
+def clear_of_degenerate(o, live):
+    """Live pixels whose smallest eigenvalue is separated (GAP_MIN), and how
+    many live pixels were left out."""
+    lam = np.abs(np.nan_to_num(np.asarray(o["lam"], np.float64), nan=1.0))
+    clear = live & (np.asarray(o["gap"]) > GAP_MIN * lam)
+    return clear, int(np.sum(live) - np.sum(clear))

@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from paper_2511_12051_gb300 import synth
-from parity_util import PHASE_TOL, TCOH_TOL, phase_report, to_np, wrapped_diff
+from parity_util import clear_of_degenerate, PHASE_TOL, TCOH_TOL, phase_report, to_np, wrapped_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +61,7 @@ def test_batch_uneven_stacks_match_oracle(ctx, plk):
         n_fp64 += int(np.sum(st_g == plk.PX_EMI_FP64))
         live = o["status"] != 3
         assert np.array_equal(st_g == plk.PX_NODATA, ~live)
-        clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+        clear = clear_of_degenerate(o, live)[0]
         rep = phase_report(to_np(o_g["phase"]), o["phase"], clear)
         assert rep["max"] <= PHASE_TOL, (z.shape[0], rep)
         assert np.all(to_np(o_g["phase"])[ref][live] == 0.0)

@@ -16,7 +16,7 @@ import torch
 
 import oracle
 from paper_2511_12051_gb300 import synth
-from parity_util import PHASE_TOL, TCOH_TOL, phase_report, to_np
+from parity_util import clear_of_degenerate, PHASE_TOL, TCOH_TOL, phase_report, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_regularised_phase_link_parity(plk, ctx, cfg, N, win, beta, ref):
     ph, tc, st = to_np(g["phase"]), to_np(g["tcoh"]), to_np(g["status"])
     live = o["status"] != 3
     assert np.array_equal(st == 3, ~live)
-    clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+    clear = clear_of_degenerate(o, live)[0]
     assert clear.sum() >= 0.98 * live.sum()
     rep = phase_report(ph, o["phase"], clear)
     print(f"beta={beta}, N={N}: phase {rep}, EVD fallback {np.sum(o['status'] == 2)} of {live.sum()}")
@@ -73,7 +73,7 @@ def test_shift_above_or_below_lambda_min(plk, ctx, mu):
     g = ctx.phase_link(torch.from_numpy(C).cuda(), N, ref, plk.default_params(mu=mu))
     ph, st = to_np(g["phase"]), to_np(g["status"])
     live = o["status"] != 3
-    clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0))) & (st != 4)
+    clear = clear_of_degenerate(o, live)[0] & (st != 4)
     assert clear.sum() >= 0.98 * live.sum()
     rep = phase_report(ph, o["phase"], clear)
     print(f"mu={mu}: phase {rep}, not converged {np.sum(st == 4)}")

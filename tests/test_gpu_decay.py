@@ -14,7 +14,7 @@ import torch
 
 import oracle
 from paper_2511_12051_gb300 import synth
-from parity_util import PHASE_TOL, TCOH_TOL, count_np, phase_report, to_np, write_state_file
+from parity_util import clear_of_degenerate, PHASE_TOL, TCOH_TOL, count_np, phase_report, to_np, write_state_file
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +65,7 @@ def test_decaying_chain_per_step(plk, ctx, lam, tmp_path):
         assert np.array_equal(count_np(g["count"]), o["count"]), k
         live = o["status"] != 3
         assert np.array_equal(to_np(g["status"]) == 3, ~live)
-        clear = live & (o["gap"] > 1e-6 * np.abs(np.nan_to_num(o["lam"], nan=1.0)))
+        clear = clear_of_degenerate(o, live)[0]
         rep = phase_report(to_np(g["phase"]), o["phase"][o["K_used"]:], clear)
         assert rep["max"] <= PHASE_TOL, (k, rep)
         assert np.abs(to_np(g["tcoh"]) - o["tcoh"])[live].max() <= TCOH_TOL

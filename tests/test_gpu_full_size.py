@@ -23,7 +23,7 @@ import torch
 
 import oracle
 from paper_2511_12051_gb300 import synth
-from parity_util import PHASE_TOL, TCOH_TOL, count_np, to_np, wrapped_diff
+from parity_util import GAP_MIN, PHASE_TOL, TCOH_TOL, count_np, to_np, wrapped_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -98,7 +98,7 @@ def test_sampled_output_pixels_at_full_size(burst):
         if g_status == 4:        # not converged: no unique answer to compare
             continue
         assert (g_status == 2) == (o["status"] == 2), (oy, ox, g_status, o["status"])
-        if o["gap"] > 1e-6 * abs(o["lam"] if np.isfinite(o["lam"]) else 1.0):
+        if o["gap"] > GAP_MIN * abs(o["lam"] if np.isfinite(o["lam"]) else 1.0):
             d = wrapped_diff(burst["phase"][:, oy, ox], o["phase"]).max()
             worst = max(worst, d)
             n_clear += 1
@@ -233,7 +233,7 @@ def test_batch_sampled_at_full_size(plk):
             assert (st[oy, ox] == 2) == (o["status"] == 2), (i, oy, ox)
             n_fp64 += int(st[oy, ox] == 1)
             n_evd += int(st[oy, ox] == 2)
-            if o["gap"] > 1e-6 * abs(o["lam"] if np.isfinite(o["lam"]) else 1.0):
+            if o["gap"] > GAP_MIN * abs(o["lam"] if np.isfinite(o["lam"]) else 1.0):
                 d = wrapped_diff(ph[:, oy, ox], o["phase"]).max()
                 diffs.append(d)
                 assert d <= PHASE_TOL, (i, oy, ox, d)
