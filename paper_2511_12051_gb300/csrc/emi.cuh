@@ -443,9 +443,15 @@ __device__ __forceinline__ bool inverse_iteration(cpx<T> (&a)[NP], cpx<T> &x, cp
 // is first order and loose (on synthetic stacks the measured single-precision
 // error sits three to four orders of magnitude below it), so pixels are handed
 // to double precision when it exceeds err_max (default 0.1).
-template <int NP, class T, class Loader>
+//
+// GSM = true: once inverted, this lane's row of G^{-1} moves to gslot (NP
+// values, 16-byte aligned, private to the lane) and is read back where it is
+// used -- each rebuild of B^{-1} and the residual correction -- instead of
+// holding NP registers through the complex elimination and the iteration.
+template <int NP, class T, class Loader, bool GSM = false>
 __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, const EmiParams &prm,
-                                 cpx<T> *cbuf, unsigned gmask, int glane0, bool is_fp64) {
+                                 cpx<T> *cbuf, unsigned gmask, int glane0, bool is_fp64, T *gslot = nullptr) {
+    static_assert(!GSM || (NP * sizeof(T)) % 16 == 0, "G^-1 row slot: whole 16-byte chunks");
     PixelResult out;
     out.flag = false;
     T *rbuf = reinterpret_cast<T *>(cbuf);
@@ -496,6 +502,33 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         return out;
     }
     const bool inv_failed = clear_fail || (minpiv <= pfail) || !finite;
+    // G^{-1} row: kept in g, or parked in gslot (GSM) and read back by with_g.
+    auto put_g = [&](const T (&src)[NP]) {
+        if constexpr (GSM) {
+            constexpr int E = 16 / sizeof(T);
+#pragma unroll
+            for (int q = 0; q < NP / E; ++q) {
+                uint4 v;
+                memcpy(&v, &src[q * E], 16);
+                reinterpret_cast<uint4 *>(gslot)[q] = v;
+            }
+        }
+    };
+    auto with_g = [&](auto &&f) {
+        if constexpr (GSM) {
+            constexpr int E = 16 / sizeof(T);
+            T gg[NP];
+#pragma unroll
+            for (int q = 0; q < NP / E; ++q) {
+                const uint4 v = reinterpret_cast<const uint4 *>(gslot)[q];
+                memcpy(&gg[q * E], &v, 16);
+            }
+            return f(gg);
+        } else {
+            return f(g);
+        }
+    };
+    put_g(g);
 
     T mu = T(prm.mu);
     if (inv_failed) load_crow<NP, T>(a, load, r, n);  // EVD fallback: power iteration on C first
@@ -511,7 +544,9 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     const T tol = is_fp64 ? T(1e-9) : T(prm.tol);
     cpx<T> d;
     T q;
-    auto reform = [&](T m) { return form_shift_inverse<NP, T>(a, g, load, m, cbuf, r, n, gmask); };
+    auto reform = [&](T m) {
+        return with_g([&](const T (&gg)[NP]) { return form_shift_inverse<NP, T>(a, gg, load, m, cbuf, r, n, gmask); });
+    };
     // Pass 0: EMI (shifted inverse iteration on A = G^-1 o C), or on the EVD
     // fallback power iteration on C.  Power iteration converges like
     // lambda_2 / lambda_1 = q; when that is slow its stopping rule leaves an
@@ -542,6 +577,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         const T cn = group_max<NP, T>(live ? cs : T(0), gmask);
 #pragma unroll
         for (int k = 0; k < NP; ++k) g[k] = T(-1);
+        put_g(g);
         mu = -(rho + T(0.1) * fmax(T(1) - q, T(0.01)) * rho);
         fl_num = -T(1.001) * cn;
         fl_den = T(1);
@@ -552,7 +588,8 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         // Residual correction against A itself: x <- x - B^{-1} (A x - rho x).
         // Its fixed point is an exact eigenvector of A, whatever the rounding
         // of the computed B^{-1} (preconditioned inverse iteration).
-        const cpx<T> ax = apply_A<NP, T>(g, load, x, cbuf, r, n, gmask);
+        const cpx<T> ax =
+            with_g([&](const T (&gg)[NP]) { return apply_A<NP, T>(gg, load, x, cbuf, r, n, gmask); });
         const T rho = group_sum<NP, T>(live ? (x.x * ax.x + x.y * ax.y) : T(0), gmask);
         const cpx<T> res = live ? (ax - rho * x) : mk<T>(T(0), T(0));
         cpx<T> corr = group_matvec<NP, T>(a, res, cbuf, r, gmask);

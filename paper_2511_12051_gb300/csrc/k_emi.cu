@@ -117,9 +117,17 @@ __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool 
 // Rows of 24 entries (17 <= N <= 24) run one pixel a warp with lanes 24-31
 // idle: fewer registers than 32-entry rows (three CTAs an SM instead of two)
 // and a quarter fewer updates per elimination step.
+// Warps per CTA of the single-precision pass: 2 for rows of 24 and 32
+// entries, whose per-lane shared memory would otherwise pass the 48 KB a CTA
+// may declare statically.  CTAs per SM: 6 of 2 warps for those (168 and 160
+// registers, with the G^{-1} row in shared memory; 244 and 168 without).
+template <int NP>
+struct EmiWarps {
+    static constexpr int value = NP >= 24 ? 2 : 4;
+};
 template <int NP>
 struct EmiMinBlocks {
-    static constexpr int value = NP == 32 ? 1 : (NP == 24 ? 3 : PLK_EMI_MINB);
+    static constexpr int value = NP >= 24 ? 6 : PLK_EMI_MINB;
 };
 
 // 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (the
@@ -144,26 +152,31 @@ struct EmiPrefetch {
 };
 
 template <int NP>
-__global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi32(const float2 *__restrict__ C, int n, long long npx,
+__global__ void __launch_bounds__(EmiWarps<NP>::value * 32, EmiMinBlocks<NP>::value) k_emi32(const float2 *__restrict__ C, int n, long long npx,
                                                           int ref, const EmiParams prm,
                                                           float *__restrict__ phase, float *__restrict__ tcoh,
                                                           float *__restrict__ lam, uint8_t *__restrict__ status,
                                                           bool use_list) {
     constexpr bool kPow2 = (NP & (NP - 1)) == 0;
+    constexpr int kW = EmiWarps<NP>::value;
     constexpr int G = kPow2 ? 32 / NP : 1;
     constexpr bool kPf = EmiPrefetch<NP>::on;
     // Complex entries per cached row: NP + 2 (16-byte aligned rows whose
     // 16-byte chunks fall in different banks for 8 consecutive lanes).
     constexpr int kRowPitch = NP + 2;
-    __shared__ __align__(16) cpx<float> sbuf[kEmiWarps][32];
-    __shared__ __align__(16) cpx<float> rowcache[kEmiWarps * 32 * kRowPitch];
-    __shared__ __align__(16) float2 pf[kEmiWarps][kPf ? 2 : 1][EmiPrefetch<NP>::elems];
+    __shared__ __align__(16) cpx<float> sbuf[kW][32];
+    __shared__ __align__(16) cpx<float> rowcache[kW * 32 * kRowPitch];
+    __shared__ __align__(16) float2 pf[kW][kPf ? 2 : 1][EmiPrefetch<NP>::elems];
+    // Rows of G^{-1}, one per lane; the pitch NP + 4 puts the 16-byte chunks of
+    // 8 consecutive lanes in different banks.
+    constexpr int kGPitch = NP + 4;
+    __shared__ __align__(16) float gsm[kW * 32 * kGPitch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
     const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
-    const long long step = (long long)gridDim.x * kEmiWarps * G;
+    const long long step = (long long)gridDim.x * kW * G;
     cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
 
     // Copy the packed triangles of pixels b .. b + G - 1 (those below npx)
@@ -179,7 +192,7 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
             cp_async_commit();
         }
     };
-    long long base = ((long long)blockIdx.x * kEmiWarps + warp) * G;
+    long long base = ((long long)blockIdx.x * kW + warp) * G;
     int slot = 0;
     prefetch(base, 0);
     for (; base < npx; base += step, slot ^= 1) {
@@ -227,7 +240,8 @@ __global__ void __launch_bounds__(kEmiWarps * 32, EmiMinBlocks<NP>::value) k_emi
                 }
             }
             SmemRow<NP> ld{myrow};
-            const PixelResult res = emi_solve<NP, float>(ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0, false);
+            const PixelResult res = emi_solve<NP, float, SmemRow<NP>, true>(
+                ld, r, n, ref, prm, &sbuf[warp][glane0], gmask, glane0, false, gsm + (warp * 32 + lane) * kGPitch);
             if (res.flag) {
                 if (r == 0) {
                     status[p] = (uint8_t)kPending;
@@ -398,14 +412,15 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
                            const StackSource *src) {
     constexpr int G = (NP & (NP - 1)) ? 1 : 32 / NP;
     constexpr int NP64 = (NP & (NP - 1)) ? 32 : NP;  // the double-precision re-solve keeps power-of-two groups
-    const long long cap = (long long)device_sm_count() * 16;
-    long long blocks = ((npx + G - 1) / G + kEmiWarps - 1) / kEmiWarps;
+    constexpr int W = EmiWarps<NP>::value;
+    const long long cap = (long long)device_sm_count() * 64 / W;
+    long long blocks = ((npx + G - 1) / G + W - 1) / W;
     blocks = blocks > cap ? cap : (blocks < 1 ? 1 : blocks);
     // pixel indices of the pending list are 32-bit
     const bool use_list = npx <= 0xffffffffLL;
     if (prm.fp64_resolve) k_reset_counter<<<1, 32, 0, s>>>(prm.work);
     if (prof) prof->begin("phase_link_fp32", s);
-    k_emi32<NP><<<(unsigned)blocks, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status,
+    k_emi32<NP><<<(unsigned)blocks, W * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status,
                                                            use_list && prm.fp64_resolve);
     cudaError_t e = cudaGetLastError();
     if (prof) prof->end(s);
