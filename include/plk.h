@@ -489,6 +489,43 @@ plk_status plk_batch_destroy(plk_batch *b);
 plk_status plk_tuned_schedule(const plk_ctx *ctx, int N, plk_window win, int *cov_tile_y, int *cov_tile_x,
                               int *emi_lanes);
 
+/* ------------------------------------------------------ spatial tiles */
+
+/* One spatial tile of a burst, for independent processes (one per GPU or per
+ * job; the path needs no exchange between them).  Output pixels depend only on
+ * the samples of their SHP window (Sec. III-A) and, along the sequential chain,
+ * on the compressed SLCs of earlier mini-stacks in that window (Sec. II-B), so
+ * a tile is processed from an input crop that holds its cells' windows: a
+ * read-only halo, one window wider for every further mini-stack step.
+ *   y0, x0, h, w      the input crop: burst rows y0 .. y0+h-1, columns
+ *                     x0 .. x0+w-1 (y0, x0 multiples of the strides, so the
+ *                     crop's output cells are the burst's);
+ *   oy0, ox0, oh, ow  the owned output cells of the burst's grid;
+ *   cy0, cx0          where the owned cells sit in the crop's output grid
+ *                     (burst cell oy0 + i is crop cell cy0 + i);
+ *   py0, px0, ph, pw  the owned full-resolution pixels: the owned cells'
+ *                     decimation blocks (the last cell row/column's running
+ *                     to the image end), where the crop's compressed SLC
+ *                     equals the burst's. */
+typedef struct plk_tile {
+    int32_t y0, x0, h, w;
+    int32_t oy0, ox0, oh, ow;
+    int32_t cy0, cx0;
+    int32_t py0, px0, ph, pw;
+} plk_tile;
+/* Split the Ho x Wo output grid of an H x W burst into tiles_y x tiles_x tiles
+ * of near-equal cell counts (tiles[ty * tiles_x + tx], host memory) and give
+ * each the smallest crop, grown a stride at a time, on which a state that
+ * runs `steps` mini-stack steps (plk_ministack_step on the crops of the same
+ * SLCs, same window and parameters) produces, on the owned cells, the burst's
+ * phases, gamma_t, statuses and SHP counts at every step, and on the owned
+ * pixels its compressed SLCs (a cell is exact when its window, clipped to the
+ * burst, lies in the crop, its decimation block is the same in both, and its
+ * window's compressed SLCs were exact at every earlier step).  Host only.
+ * Errors: EINVAL (no tiles, more tiles than output cells along an axis,
+ * steps < 1, bad window). */
+plk_status plk_tile_plan(int H, int W, plk_window win, int tiles_y, int tiles_x, int steps, plk_tile *tiles);
+
 /* ------------------------------------------- allocation-free variant */
 
 /* Scratch capacity of plk_phase_link_stack_noalloc, in bytes: one array of

@@ -7,7 +7,7 @@
 struct plk_ctx {
     int device;
     cudaStream_t stream;
-    unsigned long long *work;  // device counter of the FP64 re-solve
+    unsigned long long *work;  // work area of the FP64 re-solve (plk::kEmiWorkBytes)
     char err[512];
     plk::Prof prof;
     // aggregated by plk_profile_collect
@@ -30,7 +30,7 @@ plk_status cuda_fail(plk_ctx *ctx, cudaError_t e, const char *what);
 bool window_ok(plk_window w);
 inline bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 // The checks every entry point applies to plk_params, and the kernel
-// parameters they resolve to (work: the device counter of the re-solve).
+// parameters they resolve to (work: the work area of the re-solve).
 bool params_ok(const plk_params &p);
 void emi_params(const plk_params &p, unsigned long long *work, plk::EmiParams *out);
 // plk_params (NULL = defaults) -> kernel parameters, GLRT size and coherence precision.

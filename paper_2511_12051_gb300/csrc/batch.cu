@@ -24,7 +24,7 @@ struct plk_batch {
         uint64_t *mask;            // [Ho][Wo][nwords]
         uint16_t *count;           // [Ho][Wo]
         float2 *C;                 // [Ho][Wo][ntri(N)]
-        unsigned long long *work;  // this stack's FP64 re-solve counter
+        unsigned long long *work;  // this stack's FP64 re-solve work area
         double cost;               // relative work, for the stream assignment
         int stream;
     };

@@ -1,8 +1,12 @@
-"""Multi-GPU plumbing for independent work units (bursts or stacks).
+"""Multi-GPU plumbing for independent work units (bursts, stacks or spatial
+tiles of one burst).
 
 The phase-linking path shards without any data exchange: each rank processes
 its own units and the only collectives are timing ones (a barrier and the
 maximum of the per-rank times).  Works with NCCL on GPUs and gloo on CPU.
+Spatial tiles come from plk_tile_plan (plk.tile_plan): each tile's crop holds
+its owned cells' windows for the planned number of mini-stack steps, so a rank
+runs an ordinary state on the crop and keeps the owned part.
 """
 from __future__ import annotations
 
@@ -42,3 +46,18 @@ def max_over_ranks(value: float, device: torch.device | str = "cpu") -> float:
 def barrier() -> None:
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         dist.barrier()
+
+
+def tile_slices(t: dict) -> dict:
+    """Index tuples of a plk_tile_plan tile: 'crop' (rows, columns of the burst
+    the tile loads), 'cells' / 'burst_cells' (its owned output cells in the
+    crop's and in the burst's output grid), 'pixels' / 'burst_pixels' (its owned
+    full-resolution pixels in the crop and in the burst)."""
+    return {
+        "crop": (slice(t["y0"], t["y0"] + t["h"]), slice(t["x0"], t["x0"] + t["w"])),
+        "cells": (slice(t["cy0"], t["cy0"] + t["oh"]), slice(t["cx0"], t["cx0"] + t["ow"])),
+        "burst_cells": (slice(t["oy0"], t["oy0"] + t["oh"]), slice(t["ox0"], t["ox0"] + t["ow"])),
+        "pixels": (slice(t["py0"] - t["y0"], t["py0"] - t["y0"] + t["ph"]),
+                   slice(t["px0"] - t["x0"], t["px0"] - t["x0"] + t["pw"])),
+        "burst_pixels": (slice(t["py0"], t["py0"] + t["ph"]), slice(t["px0"], t["px0"] + t["pw"])),
+    }

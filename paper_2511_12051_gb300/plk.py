@@ -50,6 +50,11 @@ class StackDesc(ctypes.Structure):
                 ("status", ctypes.c_void_p)]
 
 
+class Tile(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("y0", "x0", "h", "w", "oy0", "ox0", "oh", "ow", "cy0", "cx0",
+                                                "py0", "px0", "ph", "pw")]
+
+
 COV_FP32 = 0  # PLK_COV_FP32
 COV_BF16 = 1  # PLK_COV_BF16
 COV_FP16 = 2  # PLK_COV_FP16
@@ -108,6 +113,7 @@ _SIGS = {
     "plk_batch_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "plk_batch_destroy": [_P],
     "plk_tuned_schedule": [_P, _I, Window, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "plk_tile_plan": [_I, _I, Window, _I, _I, _I, ctypes.POINTER(Tile)],
 }
 EXPORTS = sorted(list(_SIGS) + ["plk_last_error", "plk_mask_words", "plk_device_allocations"])
 
@@ -165,6 +171,15 @@ def glrt_threshold_looks(alpha: float, nu: float) -> float:
     c = ctypes.c_double()
     _check(lib().plk_glrt_threshold_looks(float(alpha), float(nu), ctypes.byref(c)))
     return c.value
+
+
+def tile_plan(H: int, W: int, win, tiles_y: int, tiles_x: int, steps: int = 1) -> list[dict]:
+    """plk_tile_plan: tiles_y x tiles_x spatial tiles of an H x W burst (row-major),
+    each with the input crop that makes its owned outputs exact for `steps`
+    mini-stack steps."""
+    arr = (Tile * (int(tiles_y) * int(tiles_x)))()
+    _check(lib().plk_tile_plan(int(H), int(W), window(win), int(tiles_y), int(tiles_x), int(steps), arr))
+    return [{k: int(getattr(t, k)) for k, _ in Tile._fields_} for t in arr]
 
 
 def device_allocations() -> int:

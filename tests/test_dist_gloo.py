@@ -67,3 +67,73 @@ def test_two_gloo_ranks_shard_and_reduce():
         ch = oracle.OracleChain(12, 14, (3, 5, 1, 1), K_max=2)
         want = ch.step(synth.generate(spec).numpy())["phase_real"]
         assert np.array_equal(merged[u], want)
+
+
+# One burst split into spatial tiles (plk_tile_plan) over two gloo ranks: each
+# rank runs the oracle chain on its tiles' crops and keeps the owned parts; the
+# stitched burst equals the oracle chain run on the whole burst at every step.
+TILE_CASE = dict(H=40, W=66, win=(5, 11, 1, 1), tiles=(2, 3), T=20, M=10, K_max=2)
+
+
+def _tile_worker(rank, world, port, tiles, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    from paper_2511_12051_gb300 import synth
+    c = TILE_CASE
+    z = synth.generate(synth.config_spec(0, N=c["T"], H=c["H"], W=c["W"], seed=33)).numpy()
+    mine = {}
+    for i in pdist.shard(len(tiles), rank, world):
+        sl = pdist.tile_slices(tiles[i])
+        crop = np.ascontiguousarray(z[(slice(None),) + sl["crop"]])
+        ch = oracle.OracleChain(crop.shape[1], crop.shape[2], c["win"], K_max=c["K_max"], kappa_dtype=np.complex64)
+        steps = []
+        for s in synth.ministack_slices(c["T"], c["M"]):
+            o = ch.step(crop[s])
+            steps.append((o["phase_real"][(Ellipsis,) + sl["cells"]], o["tcoh"][sl["cells"]],
+                          ch.ring[-1][sl["pixels"]]))
+        mine[i] = steps
+    t = pdist.max_over_ranks(1.0 + rank)
+    pdist.barrier()
+    out.put((rank, t, mine))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_one_burst_into_tiles():
+    from paper_2511_12051_gb300 import build, plk
+    import oracle
+    from paper_2511_12051_gb300 import synth
+    build.build()
+    c = TILE_CASE
+    n_steps = len(synth.ministack_slices(c["T"], c["M"]))
+    tiles = plk.tile_plan(c["H"], c["W"], c["win"], *c["tiles"], n_steps)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port, world = _free_port(), 2
+    procs = [ctx.Process(target=_tile_worker, args=(r, world, port, tiles, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(t == float(world) for _, t, _ in res)
+    got = {}
+    for _, _, mine in res:
+        got.update(mine)
+    assert sorted(got) == list(range(len(tiles)))
+    z = synth.generate(synth.config_spec(0, N=c["T"], H=c["H"], W=c["W"], seed=33)).numpy()
+    ch = oracle.OracleChain(c["H"], c["W"], c["win"], K_max=c["K_max"], kappa_dtype=np.complex64)
+    for s, sl_t in enumerate(synth.ministack_slices(c["T"], c["M"])):
+        o = ch.step(z[sl_t])
+        phase = np.full_like(o["phase_real"], np.inf)
+        kappa = np.full_like(ch.ring[-1], np.inf)
+        for i, t in enumerate(tiles):
+            sl = pdist.tile_slices(t)
+            ph, tc, ka = got[i][s]
+            phase[(Ellipsis,) + sl["burst_cells"]] = ph
+            assert np.array_equal(tc, o["tcoh"][sl["burst_cells"]], equal_nan=True)
+            kappa[sl["burst_pixels"]] = ka
+        assert np.array_equal(phase, o["phase_real"], equal_nan=True)
+        assert np.array_equal(kappa, ch.ring[-1])
