@@ -479,6 +479,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="plk", choices=["plk", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-e2e-ci16", action="store_true",
+                    help="leave out the host-buffer step with complex 16-bit input")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=None,
@@ -625,6 +627,7 @@ def main():
     # status back to pinned host memory; a step's copy overlaps the previous
     # step's compute inside the library.
     e2e = None
+    e2e_ci16 = None
     if not args.no_e2e:
         zh = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
         zh.copy_(z)
@@ -673,7 +676,50 @@ def main():
                "first_step_ms": iv[0], "steady_median_ms": steady, "compute_alone_ms": ms_step,
                "intervals_ms": [round(v, 1) for v in iv],
                "h2d_link_gbs": link_gbs, "input_copy_bound_ms": bi / (link_gbs * 1e9) * 1e3}
-        del zh, oh
+        del zh
+
+        # The same through plk_ministack_step_host_ci16: the SLCs as complex
+        # 16-bit integers (Sentinel-1's sample format), half the bytes over
+        # the host link, widened on the device.  The workload quantised once,
+        # outside the timed region: round(2048 z) (|z| stays below 16 here).
+        e2e_ci16 = None
+        if not args.no_e2e_ci16:
+            with torch.cuda.stream(stream):
+                qd = torch.stack([torch.round(z.real * 2048.0), torch.round(z.imag * 2048.0)], dim=-1)
+                qd = qd.clamp_(-32768, 32767).to(torch.int16)
+            torch.cuda.synchronize(dev)
+            qh = torch.empty(qd.shape, dtype=torch.int16, pin_memory=True)
+            qh.copy_(qd)
+            del qd
+            bq = qh.numel() * qh.element_size()
+            st.enable_host_io_ci16()
+
+            def e2e_step16():
+                st.reset()
+                st.step_host_ci16(qh, params, out=oh)
+
+            e2e_step16()
+            ctx.sync()
+            torch.cuda.synchronize(dev)
+            pdist.barrier()
+            fq = [torch.cuda.Event(enable_timing=True) for _ in range(ne + 1)]
+            fq[0].record(stream)
+            for i in range(ne):
+                e2e_step16()
+                fq[i + 1].record(stream)
+            ctx.sync()
+            torch.cuda.synchronize(dev)
+            ms_q = pdist.max_over_ranks(fq[0].elapsed_time(fq[ne]), dev)
+            ivq = [fq[i].elapsed_time(fq[i + 1]) for i in range(ne)]
+            e2e_ci16 = {"value": npx * world * ne / (ms_q / 1e3), "unit": UNIT, "h2d_bytes_per_step": bq,
+                        "d2h_bytes_per_step": bo, "steps": ne, "ms_per_step": ms_q / ne,
+                        "first_step_ms": ivq[0],
+                        "steady_median_ms": sorted(ivq[1:])[len(ivq[1:]) // 2] if ne > 1 else ivq[0],
+                        "intervals_ms": [round(v, 1) for v in ivq],
+                        "input": "complex int16 samples round(2048 z) of the same workload, widened exactly on "
+                                 "the device (plk_ministack_step_host_ci16)"}
+            del qh
+        del oh
 
     # ------------------------- other modes of the same step, timed beside it
     def time_mode(alt):
@@ -807,6 +853,7 @@ def main():
             "step_roofline": step_roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_ci16": e2e_ci16,
             "gpu_launches": launches,
             "clocks": clk,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kernels.items()},

@@ -331,6 +331,25 @@ int64_t plk_device_allocations(void);
 plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
                                    const plk_params *params, float *phase, float *tcoh, uint8_t *status,
                                    uint16_t *shp_count);
+/* Set-up for plk_ministack_step_host_ci16: plk_state_enable_host_io's
+ * buffers plus two device staging buffers of M_max planes of H x W complex
+ * 16-bit samples.  A second call does nothing.  Errors: EINVAL, ENOMEM
+ * (nothing is kept). */
+plk_status plk_state_enable_host_io_ci16(plk_ctx *ctx, plk_state *st);
+/* plk_ministack_step_host with the new SLCs as complex 16-bit integers:
+ * new_slc [M][H][W][2] int16 (re, im interleaved, 4-byte aligned; the sample
+ * format Sentinel-1 SLC products store), half the bytes of complex64 over the
+ * host link.  On the device each sample is widened exactly to complex64 (every
+ * int16 is a float: no scale), so the results equal those of
+ * plk_ministack_step on the widened samples.  The samples go to one of two
+ * int16 staging buffers on the library's copy stream; the widening runs on
+ * ctx's stream before the step, and frees the buffer for the next call's copy.
+ * Needs plk_state_enable_host_io_ci16 on st (EINVAL otherwise).  Asynchronous
+ * as plk_ministack_step_host.  Errors: EINVAL, ECUDA, and those of
+ * plk_ministack_step.  Not part of the paper's method: an input format. */
+plk_status plk_ministack_step_host_ci16(plk_ctx *ctx, plk_state *st, const int16_t *new_slc, int M,
+                                        const plk_params *params, float *phase, float *tcoh, uint8_t *status,
+                                        uint16_t *shp_count);
 
 
 /* ------------------------------------------ persistent scatterers */

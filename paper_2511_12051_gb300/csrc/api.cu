@@ -41,6 +41,11 @@ struct plk_state {
         cudaStream_t copy;
         cudaEvent_t copied[2];     // stage[b] holds the call's SLCs
         cudaEvent_t released[2];   // the last step reading stage[b] has run
+        // complex 16-bit input (plk_state_enable_host_io_ci16): the samples
+        // land in stage16[b] and are widened into stage[b] on the compute stream
+        bool ready16;
+        int16_t *stage16[2];       // [M_max][H][W][2] each
+        cudaEvent_t widened[2];    // stage16[b] has been widened (free for the next copy)
     } io;
 };
 
@@ -695,6 +700,11 @@ static void state_free(plk_state *st) {
         cudaFree(st->io.count);
         cudaStreamDestroy(st->io.copy);
     }
+    if (st->io.ready16)
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(st->io.stage16[b]);
+            cudaEventDestroy(st->io.widened[b]);
+        }
     delete st;
 }
 
@@ -1055,33 +1065,19 @@ plk_status plk_state_enable_host_io(plk_ctx *ctx, plk_state *st) {
 
 int64_t plk_device_allocations(void) { return plk::g_device_allocations.load(std::memory_order_relaxed); }
 
-plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
-                                   const plk_params *params, float *phase, float *tcoh, uint8_t *status,
-                                   uint16_t *shp_count) {
-    if (!ctx) return fail(nullptr, PLK_EINVAL, "plk_ministack_step_host: null ctx");
-    if (!st || !new_slc || M < 1 || M > st->M_max || st->K_used + M < 2)
-        return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: bad argument");
-    if (st->device != ctx->device) return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: state on another device");
-    const long long npix = (long long)st->H * st->W;
-    const long long nout = (long long)(st->H / st->win.sy) * (st->W / st->win.sx);
-    if (nout > 0 && (!phase || !tcoh || !status)) return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: null output");
-    DeviceGuard dg(ctx->device);
+namespace {
+
+// Steps of plk_ministack_step_host[_ci16] after the call's SLCs are in
+// stage[b] (stream-ordered on ctx's stream): the step itself, the release of
+// stage[b], and the outputs' copies to host memory.
+plk_status step_from_stage(plk_ctx *ctx, plk_state *st, int b, int M, const plk_params *params, float *phase,
+                           float *tcoh, uint8_t *status, uint16_t *shp_count, const char *who) {
     auto &io = st->io;
-    if (!io.ready)
-        return fail(ctx, PLK_EINVAL, "plk_ministack_step_host: no staging; call plk_state_enable_host_io first");
-    const int b = io.next;
-    io.next ^= 1;
-    // Copy stream: wait until the step that last read stage[b] has run, then copy.
-    cudaError_t e = cudaStreamWaitEvent(io.copy, io.released[b], 0);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(io.stage[b], new_slc, (size_t)M * npix * sizeof(float2), cudaMemcpyHostToDevice, io.copy);
-    if (e == cudaSuccess) e = cudaEventRecord(io.copied[b], io.copy);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, io.copied[b], 0);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step_host: staging copy");
+    const long long nout = (long long)(st->H / st->win.sy) * (st->W / st->win.sx);
     plk_status ps = plk_ministack_step(ctx, st, reinterpret_cast<const plk_c64 *>(io.stage[b]), M, params, io.phase,
                                        io.tcoh, io.status, shp_count ? io.count : nullptr);
     if (ps != PLK_OK) return ps;
-    e = cudaEventRecord(io.released[b], ctx->stream);
+    cudaError_t e = cudaEventRecord(io.released[b], ctx->stream);
     if (e == cudaSuccess && nout > 0) {
         e = cudaMemcpyAsync(phase, io.phase, (size_t)M * nout * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess)
@@ -1092,8 +1088,102 @@ plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *n
             e = cudaMemcpyAsync(shp_count, io.count, (size_t)nout * sizeof(uint16_t), cudaMemcpyDeviceToHost,
                                 ctx->stream);
     }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step_host: output copy");
+    if (e != cudaSuccess) {
+        char what[96];
+        snprintf(what, sizeof what, "%s: output copy", who);
+        return cuda_fail(ctx, e, what);
+    }
     return PLK_OK;
+}
+
+// Argument checks shared by the two host-buffer steps.
+plk_status check_host_step(plk_ctx *ctx, plk_state *st, const void *new_slc, int M, float *phase, float *tcoh,
+                           uint8_t *status, bool need16, const char *who) {
+    if (!ctx) return fail(nullptr, PLK_EINVAL, "%s: null ctx", who);
+    if (!st || !new_slc || M < 1 || M > st->M_max || st->K_used + M < 2)
+        return fail(ctx, PLK_EINVAL, "%s: bad argument", who);
+    if (st->device != ctx->device) return fail(ctx, PLK_EINVAL, "%s: state on another device", who);
+    const long long nout = (long long)(st->H / st->win.sy) * (st->W / st->win.sx);
+    if (nout > 0 && (!phase || !tcoh || !status)) return fail(ctx, PLK_EINVAL, "%s: null output", who);
+    if (!st->io.ready || (need16 && !st->io.ready16))
+        return fail(ctx, PLK_EINVAL, "%s: no staging; call plk_state_enable_host_io%s first", who, need16 ? "_ci16" : "");
+    return PLK_OK;
+}
+
+}  // namespace
+
+plk_status plk_ministack_step_host(plk_ctx *ctx, plk_state *st, const plk_c64 *new_slc, int M,
+                                   const plk_params *params, float *phase, float *tcoh, uint8_t *status,
+                                   uint16_t *shp_count) {
+    const char *who = "plk_ministack_step_host";
+    plk_status ps = check_host_step(ctx, st, new_slc, M, phase, tcoh, status, false, who);
+    if (ps != PLK_OK) return ps;
+    DeviceGuard dg(ctx->device);
+    auto &io = st->io;
+    const long long npix = (long long)st->H * st->W;
+    const int b = io.next;
+    io.next ^= 1;
+    // Copy stream: wait until the step that last read stage[b] has run, then copy.
+    cudaError_t e = cudaStreamWaitEvent(io.copy, io.released[b], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(io.stage[b], new_slc, (size_t)M * npix * sizeof(float2), cudaMemcpyHostToDevice, io.copy);
+    if (e == cudaSuccess) e = cudaEventRecord(io.copied[b], io.copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, io.copied[b], 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step_host: staging copy");
+    return step_from_stage(ctx, st, b, M, params, phase, tcoh, status, shp_count, who);
+}
+
+plk_status plk_state_enable_host_io_ci16(plk_ctx *ctx, plk_state *st) {
+    plk_status ps = plk_state_enable_host_io(ctx, st);
+    if (ps != PLK_OK) return ps;
+    auto &io = st->io;
+    if (io.ready16) return PLK_OK;
+    DeviceGuard dg(ctx->device);
+    const size_t nb = (size_t)st->M_max * st->H * st->W * 2 * sizeof(int16_t);
+    io.stage16[0] = io.stage16[1] = nullptr;
+    io.widened[0] = io.widened[1] = nullptr;
+    bool ok = plk::dev_malloc((void **)&io.stage16[0], nb) == cudaSuccess &&
+              plk::dev_malloc((void **)&io.stage16[1], nb) == cudaSuccess;
+    for (int b = 0; ok && b < 2; ++b)
+        ok = cudaEventCreateWithFlags(&io.widened[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(io.stage16[b]);
+            if (io.widened[b]) cudaEventDestroy(io.widened[b]);
+            io.stage16[b] = nullptr;
+            io.widened[b] = nullptr;
+        }
+        cudaGetLastError();
+        return fail(ctx, PLK_ENOMEM, "plk_state_enable_host_io_ci16: cannot allocate %zu bytes of staging", 2 * nb);
+    }
+    io.ready16 = true;
+    return PLK_OK;
+}
+
+plk_status plk_ministack_step_host_ci16(plk_ctx *ctx, plk_state *st, const int16_t *new_slc, int M,
+                                        const plk_params *params, float *phase, float *tcoh, uint8_t *status,
+                                        uint16_t *shp_count) {
+    const char *who = "plk_ministack_step_host_ci16";
+    plk_status ps = check_host_step(ctx, st, new_slc, M, phase, tcoh, status, true, who);
+    if (ps != PLK_OK) return ps;
+    if ((uintptr_t)new_slc % 4) return fail(ctx, PLK_EINVAL, "%s: new_slc not 4-byte aligned", who);
+    DeviceGuard dg(ctx->device);
+    auto &io = st->io;
+    const long long n = (long long)M * st->H * st->W;  // complex samples
+    const int b = io.next;
+    io.next ^= 1;
+    // Copy stream: wait until stage16[b] has been widened for its last step, then copy.
+    cudaError_t e = cudaStreamWaitEvent(io.copy, io.widened[b], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(io.stage16[b], new_slc, (size_t)n * 2 * sizeof(int16_t), cudaMemcpyHostToDevice, io.copy);
+    if (e == cudaSuccess) e = cudaEventRecord(io.copied[b], io.copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, io.copied[b], 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step_host_ci16: staging copy");
+    // Widen into stage[b] on ctx's stream (after the step that last read it, in stream order).
+    e = plk::launch_ci16_to_c64(io.stage16[b], io.stage[b], n, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(io.widened[b], ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plk_ministack_step_host_ci16: widening");
+    return step_from_stage(ctx, st, b, M, params, phase, tcoh, status, shp_count, who);
 }
 
 }  // extern "C"

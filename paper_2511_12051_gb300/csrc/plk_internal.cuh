@@ -122,6 +122,9 @@ struct PsSelect {
 };
 // shift_date >= 0: the phases are re-referenced to that date (its phase subtracted).
 // ps on: each PS pixel is compressed on its own phases arg(z_i conj z_ref).
+// Complex 16-bit samples (re, im interleaved) -> complex64, n samples; src
+// and dst 16-byte aligned.
+cudaError_t launch_ci16_to_c64(const int16_t *src, float2 *dst, long long n, cudaStream_t s);
 cudaError_t launch_compress(const Planes &z, int n, int first_real, const Geom &g, const float *phase,
                             float2 *kappa, cudaStream_t s, int shift_date = -1, const PsSelect &ps = PsSelect());
 

@@ -96,6 +96,8 @@ _SIGS = {
     "plk_ministack_step": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_ministack_step_host": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_state_enable_host_io": [_P, _P],
+    "plk_state_enable_host_io_ci16": [_P, _P],
+    "plk_ministack_step_host_ci16": [_P, _P, _P, _I, ctypes.POINTER(Params), _P, _P, _P, _P],
     "plk_state_reset": [_P],
     "plk_profile_enable": [_P, _I],
     "plk_profile_collect": [_P, ctypes.POINTER(_I)],
@@ -601,6 +603,21 @@ class State:
                self.ctx.h)
         return out
 
+    def _host_outputs(self, M: int, out: dict | None, want_count: bool) -> dict:
+        if out is None:
+            pin = torch.cuda.is_available()
+            out = {
+                "phase": torch.empty((M, self.Ho, self.Wo), dtype=torch.float32, pin_memory=pin),
+                "tcoh": torch.empty((self.Ho, self.Wo), dtype=torch.float32, pin_memory=pin),
+                "status": torch.empty((self.Ho, self.Wo), dtype=torch.uint8, pin_memory=pin),
+                "count": torch.empty((self.Ho, self.Wo), dtype=torch.int16, pin_memory=pin) if want_count else None,
+            }
+        for key in ("phase", "tcoh", "status", "count"):
+            t = out.get(key)
+            if t is not None and (t.device.type != "cpu" or not t.is_contiguous()):
+                raise TypeError(f"{key}: expected a contiguous CPU tensor")
+        return out
+
     def enable_host_io(self):
         """Allocate the device staging of step_host (plk_state_enable_host_io)."""
         _check(lib().plk_state_enable_host_io(self.ctx.h, self.h), self.ctx.h)
@@ -617,22 +634,32 @@ class State:
         M = new_slc.shape[0]
         if tuple(new_slc.shape[1:]) != (self.H, self.W):
             raise ValueError("new_slc: wrong image size")
-        if out is None:
-            pin = torch.cuda.is_available()
-            out = {
-                "phase": torch.empty((M, self.Ho, self.Wo), dtype=torch.float32, pin_memory=pin),
-                "tcoh": torch.empty((self.Ho, self.Wo), dtype=torch.float32, pin_memory=pin),
-                "status": torch.empty((self.Ho, self.Wo), dtype=torch.uint8, pin_memory=pin),
-                "count": torch.empty((self.Ho, self.Wo), dtype=torch.int16, pin_memory=pin) if want_count else None,
-            }
-        for key in ("phase", "tcoh", "status", "count"):
-            t = out.get(key)
-            if t is not None and (t.device.type != "cpu" or not t.is_contiguous()):
-                raise TypeError(f"{key}: expected a contiguous CPU tensor")
+        out = self._host_outputs(M, out, want_count)
         p = params if params is not None else default_params()
         _check(lib().plk_ministack_step_host(self.ctx.h, self.h, ctypes.c_void_p(new_slc.data_ptr()), M,
                                              ctypes.byref(p), _ptr(out["phase"]), _ptr(out["tcoh"]),
                                              _ptr(out["status"]), _ptr(out.get("count"))), self.ctx.h)
+        return out
+
+    def enable_host_io_ci16(self):
+        """Allocate the staging of step_host_ci16 (plk_state_enable_host_io_ci16)."""
+        _check(lib().plk_state_enable_host_io_ci16(self.ctx.h, self.h), self.ctx.h)
+
+    def step_host_ci16(self, new_slc: torch.Tensor, params: Params | None = None, out: dict | None = None,
+                       want_count: bool = False) -> dict:
+        """step_host with complex 16-bit samples (plk_ministack_step_host_ci16):
+        new_slc a CPU int16 tensor [M, H, W, 2] (re, im; pinned for overlap).
+        Needs enable_host_io_ci16() first; asynchronous like step_host."""
+        if new_slc.device.type != "cpu" or new_slc.dtype != torch.int16 or not new_slc.is_contiguous():
+            raise TypeError("new_slc: expected a contiguous CPU int16 tensor")
+        M = new_slc.shape[0]
+        if tuple(new_slc.shape[1:]) != (self.H, self.W, 2):
+            raise ValueError("new_slc: expected shape [M, H, W, 2]")
+        out = self._host_outputs(M, out, want_count)
+        p = params if params is not None else default_params()
+        _check(lib().plk_ministack_step_host_ci16(self.ctx.h, self.h, ctypes.c_void_p(new_slc.data_ptr()), M,
+                                                  ctypes.byref(p), _ptr(out["phase"]), _ptr(out["tcoh"]),
+                                                  _ptr(out["status"]), _ptr(out.get("count"))), self.ctx.h)
         return out
 
     def close(self):
