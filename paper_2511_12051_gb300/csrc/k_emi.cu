@@ -71,8 +71,9 @@ __device__ __forceinline__ void append_pending(unsigned long long *work, long lo
 template <int NP, class Solve>
 __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool use_list, long long npx,
                                                  const uint8_t *status, int lane, const Solve &solve) {
-    constexpr int G = 32 / NP;
-    const int grp = lane / NP;
+    constexpr bool kPow2 = (NP & (NP - 1)) == 0;
+    constexpr int G = kPow2 ? 32 / NP : 1;  // rows of 24 entries: one pixel a warp
+    const int grp = kPow2 ? lane / NP : 0;
     const unsigned long long cnt = use_list ? *(volatile unsigned long long *)(work + 1) : ~0ull;
     if (cnt <= (unsigned long long)kPendCap) {
         const unsigned *lst = pending_list(work);
@@ -278,9 +279,10 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restri
                                                           bool use_list) {
     __shared__ __align__(16) cpx<double> sbuf[kEmiWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / NP, r = lane - grp * NP;
+    constexpr bool kPow2 = (NP & (NP - 1)) == 0;
+    const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
     for_each_pending<NP>(prm.work, use_list, npx, status, lane, [&](long long p) {
         PackedRow<double> ld{C + p * nt, n, r};
@@ -299,6 +301,22 @@ template <int NP, class T>
 struct RegRow {
     cpx<T> c[NP];
     __device__ __forceinline__ cpx<T> operator()(int k) const { return c[k]; }
+};
+
+// Double-precision row source in shared memory (one slot per lane): the
+// re-solve reads it to form A and again for the start vector and gamma_t, so
+// it holds no registers in between.
+template <int NP>
+struct SmemRowD {
+    const cpx<double> *row;
+    __device__ __forceinline__ cpx<double> operator()(int k) const { return row[k]; }
+};
+
+// Warps per CTA of the stack re-solve: 2 for rows of 24 and 32 entries, whose
+// per-lane row slots would otherwise pass the 48 KB a CTA may declare statically.
+template <int NP>
+struct Emi64Warps {
+    static constexpr int value = NP >= 24 ? 2 : 4;
 };
 
 // Sum of exact products in a pair of floats (hi + lo): the product a*b is
@@ -329,18 +347,24 @@ __device__ __forceinline__ double f2_value(const F2 &a) { return (double)a.hi + 
 // so the solve sees the coherence an FP64 reference computes instead of the
 // single-precision one.
 template <int NP>
-__global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_constant__ Planes z, const Geom g,
+__global__ void __launch_bounds__(Emi64Warps<NP>::value * 32) k_emi64_stack(const __grid_constant__ Planes z, const Geom g,
                                                                 const uint64_t *__restrict__ mask, int n,
                                                                 long long npx, int ref, const EmiParams prm,
                                                                 float *__restrict__ phase, float *__restrict__ tcoh,
                                                                 float *__restrict__ lam,
                                                                 uint8_t *__restrict__ status, bool use_list) {
     constexpr int E = 16 / sizeof(cpx<double>);
-    __shared__ __align__(16) cpx<double> sbuf[kEmiWarps][32];
+    constexpr int kW = Emi64Warps<NP>::value;
+    // Row slots with a pitch of NP + 1 entries: the 16-byte entries of 8
+    // consecutive lanes fall in different banks.
+    constexpr int kPitch = NP + 1;
+    __shared__ __align__(16) cpx<double> sbuf[kW][32];
+    __shared__ __align__(16) cpx<double> rows[kW * 32 * kPitch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / NP, r = lane - grp * NP;
+    constexpr bool kPow2 = (NP & (NP - 1)) == 0;
+    const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     for_each_pending<NP>(prm.work, use_list, npx, status, lane, [&](long long p) {
         const int oy = (int)(p / g.Wo), ox = (int)(p - (p / g.Wo) * g.Wo);
         const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
@@ -369,16 +393,17 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
                     }
                 }
             }
-        RegRow<NP, double> row;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) row.c[k] = mk<double>(f2_value(re[k]), f2_value(im[k]));
-        // normalise: C_rk = S_rk s_r s_k with s_i = 1/sqrt(S_ii) (0 when
-        // S_ii = 0), C_rr = 1; one square root per lane.
-        cpx<double> *buf = &sbuf[warp][glane0];
+        // The sums in double precision go straight to this lane's row slot,
+        // then are normalised there: C_rk = S_rk s_r s_k with s_i =
+        // 1/sqrt(S_ii) (0 when S_ii = 0), C_rr = 1; one square root per lane.
+        cpx<double> *slot = rows + (warp * 32 + lane) * kPitch;
         double d_own = 0.0;
 #pragma unroll
-        for (int k = 0; k < NP; ++k)
-            if (k == r) d_own = row.c[k].x;
+        for (int k = 0; k < NP; ++k) {
+            slot[k] = mk<double>(f2_value(re[k]), f2_value(im[k]));
+            if (k == r) d_own = f2_value(re[k]);
+        }
+        cpx<double> *buf = &sbuf[warp][glane0];
         const double s_own = (d_own > 0.0) ? 1.0 / sqrt(d_own) : 0.0;
         buf[r] = mk<double>(s_own, 0.0);
         __syncwarp(gmask);
@@ -392,11 +417,12 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64_stack(const __grid_con
             for (int e = 0; e < E; ++e) {
                 const int k = q4 * E + e;
                 const double sc = s_own * sk[e].x;
-                row.c[k] = (k == r) ? mk<double>(1.0, 0.0) : mk<double>(row.c[k].x * sc, row.c[k].y * sc);
+                const cpx<double> c = slot[k];
+                slot[k] = (k == r) ? mk<double>(1.0, 0.0) : mk<double>(c.x * sc, c.y * sc);
             }
         }
         __syncwarp(gmask);
-        const PixelResult res = emi_solve_mixed<NP>(row, r, n, ref, prm, buf, gmask, glane0);
+        const PixelResult res = emi_solve_mixed<NP>(SmemRowD<NP>{slot}, r, n, ref, prm, buf, gmask, glane0);
         if (r < n) phase[(long long)r * npx + p] = res.phase;
         if (r == 0) {
             if (tcoh) tcoh[p] = res.tcoh;
@@ -411,7 +437,7 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
                            float *tcoh, float *lam, uint8_t *status, cudaStream_t s, Prof *prof,
                            const StackSource *src) {
     constexpr int G = (NP & (NP - 1)) ? 1 : 32 / NP;
-    constexpr int NP64 = (NP & (NP - 1)) ? 32 : NP;  // the double-precision re-solve keeps power-of-two groups
+    constexpr int NP64 = NP;
     constexpr int W = EmiWarps<NP>::value;
     const long long cap = (long long)device_sm_count() * 64 / W;
     long long blocks = ((npx + G - 1) / G + W - 1) / W;
@@ -425,15 +451,19 @@ static cudaError_t run_emi(const float2 *C, int n, long long npx, int ref, const
     cudaError_t e = cudaGetLastError();
     if (prof) prof->end(s);
     if (e != cudaSuccess || !prm.fp64_resolve) return e;
-    long long blocks64 = ((npx + 31) / 32 + kEmiWarps - 1) / kEmiWarps;
-    const long long cap64 = (long long)device_sm_count() * 2;  // resident CTAs at this kernel's register use
-    blocks64 = blocks64 > cap64 ? cap64 : (blocks64 < 1 ? 1 : blocks64);
+    // CTAs of w warps, no more than are resident at the re-solve's register
+    // use (255 a thread: 8 warps an SM)
+    auto grid64 = [&](int w) {
+        const long long b = ((npx + 31) / 32 + w - 1) / w, cap = (long long)device_sm_count() * (8 / w);
+        return (unsigned)(b > cap ? cap : (b < 1 ? 1 : b));
+    };
+    constexpr int W64 = Emi64Warps<NP64>::value;
     if (prof) prof->begin("phase_link_fp64", s);
     if (src)
-        k_emi64_stack<NP64><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(*src->z, *src->g, src->mask, n, npx, ref,
+        k_emi64_stack<NP64><<<grid64(W64), W64 * 32, 0, s>>>(*src->z, *src->g, src->mask, n, npx, ref,
                                                                           prm, phase, tcoh, lam, status, use_list);
     else
-        k_emi64<NP64><<<(unsigned)blocks64, kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status,
+        k_emi64<NP64><<<grid64(kEmiWarps), kEmiWarps * 32, 0, s>>>(C, n, npx, ref, prm, phase, tcoh, lam, status,
                                                                     use_list);
     e = cudaGetLastError();
     if (prof) prof->end(s);
