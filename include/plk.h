@@ -503,8 +503,9 @@ plk_status plk_batch_run(plk_ctx *ctx, plk_batch *b);
 plk_status plk_batch_info(const plk_batch *b, int *graph_built, int *streams, int *nodes);
 plk_status plk_batch_destroy(plk_batch *b);
 /* The schedule the autotuner chose for (N, window) in ctx: coherence tile
- * (output pixels) and the EMI row length (8, 16, 24 or 32 entries; lanes per
- * pixel, except 24, which runs one pixel a warp); EINVAL if not tuned. */
+ * (output pixels) and the EMI row length (8, 16, 20, 24, 28 or 32 entries:
+ * the smallest that holds N or the next; 8 and 16 are lanes per pixel, the
+ * others run one pixel a warp); EINVAL if not tuned. */
 plk_status plk_tuned_schedule(const plk_ctx *ctx, int N, plk_window win, int *cov_tile_y, int *cov_tile_x,
                               int *emi_lanes);
 

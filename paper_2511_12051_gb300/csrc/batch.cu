@@ -264,8 +264,8 @@ cudaError_t tune(plk_ctx *ctx, const plk_batch *b, const plk_batch::Stack &k, pl
     e = plk::launch_covariance(k.z, N, k.g, k.mask, k.C, s, b->cov_precision, &best);
     if (e != cudaSuccess) return e;
     // EMI rows: the smallest that holds N, and the next wider.
-    const int np0 = N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 24 ? 24 : 32));
-    const int cands[2] = {np0, np0 == 8 ? 16 : 32};
+    const int np0 = plk::emi_row_length(N);
+    const int cands[2] = {np0, plk::emi_row_length(np0 + 1)};
     float best_ms = 1e30f;
     for (int ci = 0; ci < (np0 == 32 ? 1 : 2); ++ci) {
         const int np = cands[ci];

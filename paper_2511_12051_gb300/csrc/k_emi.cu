@@ -124,11 +124,11 @@ __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool 
 // registers, with the G^{-1} row in shared memory; 244 and 168 without).
 template <int NP>
 struct EmiWarps {
-    static constexpr int value = NP >= 24 ? 2 : 4;
+    static constexpr int value = NP > 16 ? 2 : 4;
 };
 template <int NP>
 struct EmiMinBlocks {
-    static constexpr int value = NP >= 24 ? 6 : PLK_EMI_MINB;
+    static constexpr int value = NP > 16 ? 6 : PLK_EMI_MINB;
 };
 
 // 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (the
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(EmiWarps<NP>::value * 32, EmiMinBlocks<NP>::va
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (!kPow2 || NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
     const long long step = (long long)gridDim.x * kW * G;
     cpx<float> *myrow = rowcache + (size_t)(warp * 32 + lane) * kRowPitch;
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kEmiWarps * 32) k_emi64(const float2 *__restri
     constexpr bool kPow2 = (NP & (NP - 1)) == 0;
     const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (!kPow2 || NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     const long long nt = ntri(n);
     for_each_pending<NP>(prm.work, use_list, npx, status, lane, [&](long long p) {
         PackedRow<double> ld{C + p * nt, n, r};
@@ -316,7 +316,7 @@ struct SmemRowD {
 // per-lane row slots would otherwise pass the 48 KB a CTA may declare statically.
 template <int NP>
 struct Emi64Warps {
-    static constexpr int value = NP >= 24 ? 2 : 4;
+    static constexpr int value = NP > 16 ? 2 : 4;
 };
 
 // Sum of exact products in a pair of floats (hi + lo): the product a*b is
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(Emi64Warps<NP>::value * 32) k_emi64_stack(cons
     constexpr bool kPow2 = (NP & (NP - 1)) == 0;
     const int grp = kPow2 ? lane / NP : 0, r = lane - grp * NP;
     const int glane0 = grp * NP;
-    const unsigned gmask = (NP >= 24) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
+    const unsigned gmask = (!kPow2 || NP == 32) ? 0xffffffffu : (((1u << NP) - 1u) << glane0);
     for_each_pending<NP>(prm.work, use_list, npx, status, lane, [&](long long p) {
         const int oy = (int)(p / g.Wo), ox = (int)(p - (p / g.Wo) * g.Wo);
         const int cy = oy * g.sy + g.sy / 2, cx = ox * g.sx + g.sx / 2;
@@ -476,12 +476,16 @@ cudaError_t launch_phase_link(const float2 *C, int n, long long npx, int ref, co
     if (npx == 0) return cudaSuccess;
     // Lanes per pixel: the smallest group that holds a row, unless the
     // schedule asks for a wider one (fewer pixels per warp).
-    int np = n <= 8 ? 8 : (n <= 16 ? 16 : (n <= 24 ? 24 : 32));
-    if (sch && sch->emi_np >= np && (sch->emi_np == 16 || sch->emi_np == 24 || sch->emi_np == 32)) np = sch->emi_np;
-    if (np == 8) return run_emi<8>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
-    if (np == 16) return run_emi<16>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
-    if (np == 24) return run_emi<24>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
-    return run_emi<32>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+    int np = emi_row_length(n);
+    if (sch && sch->emi_np >= np && emi_row_length(sch->emi_np) == sch->emi_np) np = sch->emi_np;
+    switch (np) {
+        case 8: return run_emi<8>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+        case 16: return run_emi<16>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+        case 20: return run_emi<20>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+        case 24: return run_emi<24>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+        case 28: return run_emi<28>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+        default: return run_emi<32>(C, n, npx, ref, prm, phase, tcoh, lam, status, s, prof, src);
+    }
 }
 
 }  // namespace plk

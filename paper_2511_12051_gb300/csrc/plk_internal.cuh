@@ -82,9 +82,17 @@ cudaError_t launch_shp(const float *sum_pow, const Geom &g, float c, uint64_t *m
 // Returns cudaErrorInvalidConfiguration if the window/N combination exceeds
 // shared memory even at a 1x1 output tile.
 // Launch schedule chosen by the batch autotuner (0 = the built-in heuristic).
+// Row length of the EMI kernels for n dates: the smallest of 8 and 16 (four
+// and two pixels a warp, NP lanes each) and 20, 24, 28 and 32 (one pixel a
+// warp) that holds n.  A solve costs about n times the row length, so the
+// intermediate rows save padded work for 17 <= n <= 28.
+__host__ __device__ inline int emi_row_length(int n) {
+    return n <= 8 ? 8 : n <= 16 ? 16 : n <= 20 ? 20 : n <= 24 ? 24 : n <= 28 ? 28 : 32;
+}
+
 struct Schedule {
     int cov_TY = 0, cov_TX = 0;  // single-precision coherence tile (output pixels)
-    int emi_np = 0;              // row length of the EMI kernels (8, 16, 24 or 32, >= n)
+    int emi_np = 0;              // row length of the EMI kernels (emi_row_length values, >= n)
 };
 
 cudaError_t launch_covariance(const Planes &z, int n, const Geom &g, const uint64_t *mask, float2 *C,

@@ -99,8 +99,9 @@ def test_batch_equals_single_stack_path_and_replays(ctx, plk):
 def test_batch_tuned_schedules(ctx, plk):
     for N in (6, 15, 21):
         s = plk.tuned_schedule(ctx, N, WIN)  # tuned by the previous tests' first runs
-        row0 = 8 if N <= 8 else (16 if N <= 16 else (24 if N <= 24 else 32))
-        assert s["emi_lanes"] in (row0, 16 if row0 == 8 else 32)
+        rows = [8, 16, 20, 24, 28, 32]  # EMI row lengths: the smallest holding N, or the next
+        i0 = next(i for i, r in enumerate(rows) if r >= N)
+        assert s["emi_lanes"] in (rows[i0], rows[min(i0 + 1, len(rows) - 1)])
         ty, tx = s["cov_tile"]
         ppw = 5 if N <= 18 else 2
         assert ty > 0 and tx > 0 and ty % ppw == 0

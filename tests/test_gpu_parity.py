@@ -97,7 +97,8 @@ def oracle_C(cfg, N, H, W, win, seed, **over):
 
 @pytest.mark.parametrize("cfg,N,ref", [(0, 10, 0), (1, 15, 0), (0, 2, 1), (0, 5, 2), (0, 16, 15), (0, 18, 3),
                                        (1, 21, 5), (0, 30, 0), (0, 32, 31),
-                                       (0, 17, 16), (0, 24, 23), (0, 25, 1)])   # edges of the 24-entry rows
+                                       (0, 17, 16), (0, 20, 19), (0, 24, 23), (0, 25, 1),
+                                       (0, 28, 27), (0, 29, 3)])   # edges of the 20-, 24- and 28-entry rows
 def test_phase_link_parity(ctx, cfg, N, ref):
     win = (5, 11, 3, 6) if cfg == 1 else (5, 11, 1, 1)
     C32 = oracle_C(cfg, N, 40, 70, win, seed=21 + N)
