@@ -2,8 +2,9 @@
 // (emi-eigenvalue-problem)), the reference phase (Sec. II-A) and the temporal
 // coherence (Sec. III-C, eq. (temporal-coherence)) of one pixel.
 //
-// A pixel is served by a group of NP lanes (NP = 8, 16 or 32 >= N); lane r owns
-// row r of every N x N matrix, held in registers.  Padded rows/columns
+// A pixel is served by a group of NP lanes (NP = 8, 16, 20, 24, 28 or 32 >= N,
+// the last four one pixel a warp); lane r owns row r of every N x N matrix,
+// held in registers.  Padded rows/columns
 // (r >= N) carry the identity and are never touched by the elimination steps.
 // Row broadcasts go through a per-group shared-memory buffer read with
 // 16-byte loads (one wavefront serves the whole group); reductions are
@@ -47,7 +48,7 @@ constexpr double kPivotFail = 1e-4;
 constexpr double kPivotBand = 2e-5;
 
 // Lanes a group's reductions span: NP when it is a power of two; otherwise
-// (rows of 24 entries) the whole warp, one pixel a warp, the lanes past the
+// (rows of 20, 24 or 28 entries) the whole warp, one pixel a warp, the lanes past the
 // last row contributing the reduction's identity (their rows are all zero, and
 // every caller passes 0, or the identity, for rows past n).
 template <int NP>

@@ -1,7 +1,7 @@
-// S4-S6 kernel over packed coherences: one NP-lane group per pixel (32/NP
-// pixels per warp), single-precision solve, and a double-precision re-solve of
-// the same pixel, inside the same group, for pixels whose |C| is
-// ill-conditioned (see emi.cuh).
+// S4-S6 kernels over packed coherences: one NP-lane group per pixel (32/NP
+// pixels a warp for NP = 8 and 16, one pixel a warp for rows of 20, 24, 28 and
+// 32 entries), a single-precision solve, and a double-precision re-solve of the
+// pixels it flags (see emi.cuh).
 #include "emi.cuh"
 
 namespace plk {
@@ -72,7 +72,7 @@ template <int NP, class Solve>
 __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool use_list, long long npx,
                                                  const uint8_t *status, int lane, const Solve &solve) {
     constexpr bool kPow2 = (NP & (NP - 1)) == 0;
-    constexpr int G = kPow2 ? 32 / NP : 1;  // rows of 24 entries: one pixel a warp
+    constexpr int G = kPow2 ? 32 / NP : 1;  // rows of 20, 24 or 28 entries: one pixel a warp
     const int grp = kPow2 ? lane / NP : 0;
     const unsigned long long cnt = use_list ? *(volatile unsigned long long *)(work + 1) : ~0ull;
     if (cnt <= (unsigned long long)kPendCap) {
@@ -115,13 +115,13 @@ __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool 
 
 // Single-precision pass: one NP-lane group per pixel.  Pixels the solve flags
 // get status kPending and no other output.
-// Rows of 24 entries (17 <= N <= 24) run one pixel a warp with lanes 24-31
-// idle: fewer registers than 32-entry rows (three CTAs an SM instead of two)
-// and a quarter fewer updates per elimination step.
-// Warps per CTA of the single-precision pass: 2 for rows of 24 and 32
-// entries, whose per-lane shared memory would otherwise pass the 48 KB a CTA
-// may declare statically.  CTAs per SM: 6 of 2 warps for those (168 and 160
-// registers, with the G^{-1} row in shared memory; 244 and 168 without).
+// Rows of 20, 24 and 28 entries (emi_row_length) run one pixel a warp with the
+// lanes past the row idle: a solve costs about n times the row length, so they
+// save the padded work of 32-entry rows for 17 <= N <= 28.
+// Warps per CTA of the single-precision pass: 2 for rows beyond 16 entries,
+// whose per-lane shared memory would otherwise pass the 48 KB a CTA may
+// declare statically.  CTAs per SM: 6 of 2 warps for those (157 to 168
+// registers, with the G^{-1} row in shared memory).
 template <int NP>
 struct EmiWarps {
     static constexpr int value = NP > 16 ? 2 : 4;
@@ -326,7 +326,7 @@ struct SmemRowD {
     __device__ __forceinline__ cpx<double> operator()(int k) const { return row[k]; }
 };
 
-// Warps per CTA of the stack re-solve: 2 for rows of 24 and 32 entries, whose
+// Warps per CTA of the stack re-solve: 2 for rows beyond 16 entries, whose
 // per-lane row slots would otherwise pass the 48 KB a CTA may declare statically.
 template <int NP>
 struct Emi64Warps {
