@@ -543,7 +543,7 @@ typedef struct plk_tile {
  * burst, lies in the crop, its decimation block is the same in both, and its
  * window's compressed SLCs were exact at every earlier step).  Host only.
  * Errors: EINVAL (no tiles, more tiles than output cells along an axis,
- * steps < 1, bad window). */
+ * steps outside 1..256, bad window). */
 plk_status plk_tile_plan(int H, int W, plk_window win, int tiles_y, int tiles_x, int steps, plk_tile *tiles);
 
 /* ------------------------------------------- allocation-free variant */

@@ -40,12 +40,13 @@ struct Axis {
 bool exact(const Axis &ax, int c0, int c1, int a, int b, int steps) {
     const int G = ax.G();
     const int first = c0 / ax.s, Gc = (c1 - c0) / ax.s;  // crop cells: burst cells first .. first + Gc - 1
-    std::vector<char> prev(G, 0), cur(G, 0);
+    if (a < first || b > first + Gc) return false;
+    // exactness of the crop's cells (index i - first); a cell outside the crop is never exact
+    std::vector<char> prev(Gc, 0), cur(Gc, 0);
     for (int step = 1; step <= steps; ++step) {
-        for (int i = 0; i < G; ++i) {
-            cur[i] = 0;
-            if (i < first || i >= first + Gc) continue;
-            const int j = i - first;
+        for (int j = 0; j < Gc; ++j) {
+            const int i = first + j;
+            cur[j] = 0;
             const int crop_hi = (j == Gc - 1) ? c1 : c0 + (j + 1) * ax.s;
             if (ax.block_lo(i) != c0 + j * ax.s || ax.block_hi(i) != crop_hi) continue;
             const int centre = i * ax.s + ax.s / 2;
@@ -56,31 +57,44 @@ bool exact(const Axis &ax, int c0, int c1, int a, int b, int steps) {
             if (step > 1)
                 for (int y = w0; y < w1 && ok; ++y) {
                     const int cell = (y / ax.s < G - 1) ? y / ax.s : G - 1;
-                    ok = prev[cell] != 0;
+                    ok = cell >= first && cell < first + Gc && prev[cell - first] != 0;
                 }
-            cur[i] = ok ? 1 : 0;
+            cur[j] = ok ? 1 : 0;
         }
         for (int i = a; i < b; ++i)
-            if (!cur[i]) return false;
-        // a compressed SLC row is exact after this step and all earlier ones
-        for (int i = 0; i < G; ++i) prev[i] = (step == 1 ? cur[i] : (prev[i] && cur[i])) ? 1 : 0;
+            if (!cur[i - first]) return false;
+        // a compressed SLC row is exact after this step and all earlier ones;
+        // once that set stops changing, every later step repeats this one
+        bool changed = step == 1;
+        for (int j = 0; j < Gc; ++j) {
+            const char v = (step == 1 ? cur[j] : (prev[j] && cur[j])) ? 1 : 0;
+            changed = changed || v != prev[j];
+            prev[j] = v;
+        }
+        if (!changed) break;
     }
     return true;
 }
 
-// The smallest crop (in steps of one stride on each side) for cells [a, b).
+// The smallest crop, grown one stride at a time on both sides, for cells
+// [a, b).  A larger crop keeps every cell a smaller one makes exact, so the
+// margin is found by bisection; the whole axis is always exact.
 void plan_axis(const Axis &ax, int a, int b, int steps, int *c0, int *c1) {
     const int lo0 = ax.block_lo(a), hi0 = ax.block_hi(b - 1);
-    for (int m = 0;; ++m) {
-        int lo = lo0 - m * ax.s, hi = hi0 + m * ax.s;
-        if (lo < 0) lo = 0;
-        if (hi > ax.L) hi = ax.L;
-        if (exact(ax, lo, hi, a, b, steps) || (lo == 0 && hi == ax.L)) {
-            *c0 = lo;
-            *c1 = hi;
-            return;
-        }
+    auto crop = [&](int m, int *lo, int *hi) {
+        *lo = lo0 - m * ax.s < 0 ? 0 : lo0 - m * ax.s;
+        *hi = hi0 + m * ax.s > ax.L ? ax.L : hi0 + m * ax.s;
+    };
+    int m_lo = 0, m_hi = (lo0 + ax.s - 1) / ax.s;
+    if ((ax.L - hi0 + ax.s - 1) / ax.s > m_hi) m_hi = (ax.L - hi0 + ax.s - 1) / ax.s;
+    while (m_lo < m_hi) {  // smallest m in [m_lo, m_hi] whose crop is exact
+        const int m = (m_lo + m_hi) / 2;
+        int lo, hi;
+        crop(m, &lo, &hi);
+        if (exact(ax, lo, hi, a, b, steps)) m_hi = m;
+        else m_lo = m + 1;
     }
+    crop(m_lo, c0, c1);
 }
 
 }  // namespace
@@ -88,7 +102,7 @@ void plan_axis(const Axis &ax, int a, int b, int steps, int *c0, int *c1) {
 extern "C" {
 
 plk_status plk_tile_plan(int H, int W, plk_window win, int tiles_y, int tiles_x, int steps, plk_tile *tiles) {
-    if (!tiles || H < 1 || W < 1 || !window_ok(win) || steps < 1 || steps > 4096)
+    if (!tiles || H < 1 || W < 1 || !window_ok(win) || steps < 1 || steps > 256)
         return fail(nullptr, PLK_EINVAL, "plk_tile_plan: bad argument");
     const Axis ay{H, win.sy, win.wy / 2}, ax{W, win.sx, win.wx / 2};
     if (tiles_y < 1 || tiles_x < 1 || tiles_y > ay.G() || tiles_x > ax.G())

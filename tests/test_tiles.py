@@ -60,6 +60,7 @@ def test_plan_halo_grows_one_window_a_step(plk):
 
 def test_plan_rejects_bad_requests(plk):
     for args in [(10, 10, (3, 3, 1, 1), 11, 1, 1), (10, 10, (3, 3, 1, 1), 1, 1, 0), (10, 10, (4, 3, 1, 1), 1, 1, 1),
+                 (10, 10, (3, 3, 1, 1), 1, 1, 257),
                  (10, 10, (3, 3, 1, 1), 0, 1, 1), (5, 10, (3, 3, 6, 1), 1, 1, 1)]:
         with pytest.raises(plk.PlkError):
             plk.tile_plan(*args)
