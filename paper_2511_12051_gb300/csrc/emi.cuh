@@ -607,14 +607,10 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
         // gap = lambda_2 - lambda_1 from q = theta / (lambda_2 - mu)
         const T gap = (q > T(0)) ? abs_t(theta) * (T(1) / q - T(1)) : abs_t(theta) * T(1e3);
         const T est = T(4) * Eps<T>::v * cond * norm_gi / fmax(gap, Lim<T>::tiny);
-#ifdef PLK_DEBUG_EST
-        out.lam = (float)est;  // diagnostic builds export the estimate instead of flagging
-#else
         if (!conv || !(est <= T(prm.err_max))) {
             out.flag = true;
             return out;
         }
-#endif
     }
 
     // Reference (Sec. II-A): phihat_i = arg(v_i conj(v_ref)), phihat_ref = 0.
@@ -647,11 +643,7 @@ __device__ PixelResult emi_solve(const Loader &load, int r, int n, int ref, cons
     out.tcoh = (float)tcoh;
     out.v = mk<float>((float)x.x, (float)x.y);
     out.evd = inv_failed;
-#ifndef PLK_DEBUG_EST
     out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
-#else
-    if (is_fp64 || inv_failed) out.lam = inv_failed ? __int_as_float(0x7fc00000) : (float)lam;
-#endif
     out.status = !conv ? PLK_PX_NOCONV : (inv_failed ? PLK_PX_EVD : (is_fp64 ? PLK_PX_EMI_FP64 : PLK_PX_EMI));
     return out;
 }

@@ -108,10 +108,6 @@ __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool 
         }
     }
 }
-// CTAs per SM the single-precision kernel is register-budgeted for (NP <= 16).
-#ifndef PLK_EMI_MINB
-#define PLK_EMI_MINB 4
-#endif
 
 // Single-precision pass: one NP-lane group per pixel.  Pixels the solve flags
 // get status kPending and no other output.
@@ -120,15 +116,16 @@ __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool 
 // save the padded work of 32-entry rows for 17 <= N <= 28.
 // Warps per CTA of the single-precision pass: 2 for rows beyond 16 entries,
 // whose per-lane shared memory would otherwise pass the 48 KB a CTA may
-// declare statically.  CTAs per SM: 6 of 2 warps for those (157 to 168
-// registers, with the G^{-1} row in shared memory).
+// declare statically.  CTAs per SM the kernel is register-budgeted for: 4 of
+// 4 warps for rows of 8 and 16 entries (at most 128 registers), 6 of 2 warps
+// beyond (157 to 168 registers, with the G^{-1} row in shared memory).
 template <int NP>
 struct EmiWarps {
     static constexpr int value = NP > 16 ? 2 : 4;
 };
 template <int NP>
 struct EmiMinBlocks {
-    static constexpr int value = NP > 16 ? 6 : PLK_EMI_MINB;
+    static constexpr int value = NP > 16 ? 6 : 4;
 };
 
 // 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (the
