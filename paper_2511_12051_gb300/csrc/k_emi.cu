@@ -137,16 +137,15 @@ __device__ __forceinline__ void cp_async8_emi(void *dst, const void *src, int sr
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-// Prefetch depth of the packed coherences: the warp copies the triangles of
-// its next G pixels (G * N(N+1)/2 entries, one contiguous run) into shared
-// memory while it solves the current ones, so the gather of a pixel's rows
-// reads shared memory instead of waiting on global loads.  Off for 32-entry
-// rows, whose two buffers would exceed the static shared-memory budget.
+// Prefetch of the packed coherences: the warp copies the triangles of its
+// next G pixels (G * N(N+1)/2 entries, one contiguous run) into shared memory
+// while it solves the current ones, so the gather of a pixel's rows reads
+// shared memory instead of waiting on global loads (two slots a warp; with the
+// two-warp CTAs of rows beyond 16 entries they fit the static budget up to 32).
 template <int NP>
 struct EmiPrefetch {
     static constexpr int G = ((NP & (NP - 1)) == 0) ? 32 / NP : 1;
-    static constexpr bool on = NP <= 24;
-    static constexpr int elems = on ? G * NP * (NP + 1) / 2 : 1;
+    static constexpr int elems = G * NP * (NP + 1) / 2;
 };
 
 template <int NP>
@@ -158,13 +157,12 @@ __global__ void __launch_bounds__(EmiWarps<NP>::value * 32, EmiMinBlocks<NP>::va
     constexpr bool kPow2 = (NP & (NP - 1)) == 0;
     constexpr int kW = EmiWarps<NP>::value;
     constexpr int G = kPow2 ? 32 / NP : 1;
-    constexpr bool kPf = EmiPrefetch<NP>::on;
     // Complex entries per cached row: NP + 2 (16-byte aligned rows whose
     // 16-byte chunks fall in different banks for 8 consecutive lanes).
     constexpr int kRowPitch = NP + 2;
     __shared__ __align__(16) cpx<float> sbuf[kW][32];
     __shared__ __align__(16) cpx<float> rowcache[kW * 32 * kRowPitch];
-    __shared__ __align__(16) float2 pf[kW][kPf ? 2 : 1][EmiPrefetch<NP>::elems];
+    __shared__ __align__(16) float2 pf[kW][2][EmiPrefetch<NP>::elems];
     // Rows of G^{-1}, one per lane; the pitch NP + 4 puts the 16-byte chunks of
     // 8 consecutive lanes in different banks.
     constexpr int kGPitch = NP + 4;
@@ -180,15 +178,13 @@ __global__ void __launch_bounds__(EmiWarps<NP>::value * 32, EmiMinBlocks<NP>::va
     // Copy the packed triangles of pixels b .. b + G - 1 (those below npx)
     // into prefetch slot `slot`; one commit group per call, empty past the end.
     auto prefetch = [&](long long b, int slot) {
-        if constexpr (kPf) {
-            const long long cnt = b < npx ? ((npx - b < G) ? (npx - b) : G) * nt : 0;
-            const float2 *src = C + (b < npx ? b : 0) * nt;
-            for (int e = lane; e < G * nt; e += 32) {
-                const bool ok = e < cnt;
-                cp_async8_emi(&pf[warp][slot][e], ok ? src + e : C, ok ? 8 : 0);
-            }
-            cp_async_commit();
+        const long long cnt = b < npx ? ((npx - b < G) ? (npx - b) : G) * nt : 0;
+        const float2 *src = C + (b < npx ? b : 0) * nt;
+        for (int e = lane; e < G * nt; e += 32) {
+            const bool ok = e < cnt;
+            cp_async8_emi(&pf[warp][slot][e], ok ? src + e : C, ok ? 8 : 0);
         }
+        cp_async_commit();
     };
     long long base = ((long long)blockIdx.x * kW + warp) * G;
     int slot = 0;
@@ -196,15 +192,10 @@ __global__ void __launch_bounds__(EmiWarps<NP>::value * 32, EmiMinBlocks<NP>::va
     for (; base < npx; base += step, slot ^= 1) {
         const long long p = base + grp;
         const bool valid = p < npx;
-        const float2 *Cpix;
-        if constexpr (kPf) {
-            prefetch(base + step, slot ^ 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");  // this iteration's copies have landed
-            __syncwarp();
-            Cpix = &pf[warp][slot][grp * nt];
-        } else {
-            Cpix = C + (valid ? p : 0) * nt;
-        }
+        prefetch(base + step, slot ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this iteration's copies have landed
+        __syncwarp();
+        const float2 *Cpix = &pf[warp][slot][grp * nt];
         bool nan = false;
         if (valid && r < n) nan = isnan(Cpix[packed_index(n, r, r)].x);
         nan = __any_sync(gmask, nan);
@@ -277,7 +268,7 @@ __global__ void __launch_bounds__(EmiWarps<NP>::value * 32, EmiMinBlocks<NP>::va
         }
         __syncwarp();  // the slot is free for the copies issued next iteration
     }
-    if constexpr (kPf) asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Double-precision re-solve of the pixels left pending, one per NP-lane group
