@@ -116,16 +116,17 @@ __device__ __forceinline__ void for_each_pending(unsigned long long *work, bool 
 // save the padded work of 32-entry rows for 17 <= N <= 28.
 // Warps per CTA of the single-precision pass: 2 for rows beyond 16 entries,
 // whose per-lane shared memory would otherwise pass the 48 KB a CTA may
-// declare statically.  CTAs per SM the kernel is register-budgeted for: 4 of
-// 4 warps for rows of 8 and 16 entries (at most 128 registers), 6 of 2 warps
-// beyond (157 to 168 registers, with the G^{-1} row in shared memory).
+// declare statically.  CTAs per SM the kernel is register-budgeted for: 16
+// warps an SM at 128 registers for rows of up to 24 entries (4 CTAs of 4 warps,
+// 8 of 2), 12 warps for 28 and 32 (6 CTAs of 2, up to 168 registers: at 128
+// they spill and run 4% slower at N = 28, while 16 warps gain 12% at N = 20).
 template <int NP>
 struct EmiWarps {
     static constexpr int value = NP > 16 ? 2 : 4;
 };
 template <int NP>
 struct EmiMinBlocks {
-    static constexpr int value = NP > 16 ? 6 : 4;
+    static constexpr int value = NP > 24 ? 6 : (NP > 16 ? 8 : 4);
 };
 
 // 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (the
